@@ -1,0 +1,82 @@
+/*
+ * CPU oracle for the Restricted Additive Schwarz (RAS) solver.
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, sequential FP64
+ * restatement of the method, used to check the CUDA path. Only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Notation (Sec. 2.1, Fig. 1): O_p = rows owned by subdomain p (the
+ * partition), Omega_p = O_p grown by `gamma` layers of graph neighbours (the
+ * overlap), E_p = points outside Omega_p coupled to it (the external
+ * interface, red points of Fig. 1). Local unknowns are Omega_p in ascending
+ * global order.
+ *
+ * Return codes: 0 ok, 1 invalid argument, 3 matrix not SPD, 4 no convergence.
+ */
+#ifndef RAS_ORACLE_H
+#define RAS_ORACLE_H
+#include <stdint.h>
+
+#define OR_OK 0
+#define OR_EINVAL 1
+#define OR_ENOTSPD 3
+#define OR_ENOCONV 4
+
+/* local solver kinds and precisions */
+#define OR_BANDCHOL 0
+#define OR_CG 1
+#define OR_ILU0_CG 2
+#define OR_FP64 0
+#define OR_FP32 1
+#define OR_BF16 2
+
+/* SplitMix64 output k (0-based) of the stream with the given seed. */
+uint64_t or_splitmix64(uint64_t seed, uint64_t k);
+/* Round a double to bfloat16 (round to nearest even) and back to double. */
+double or_round_bf16(double v);
+
+/* Partitioners (Sec. 3.2.1). */
+int or_partition_regular2d(int nx, int ny, int px, int py, int32_t *part);
+int or_partition_bfs(int n, const int32_t *rp, const int32_t *ci, int P, uint64_t seed,
+                     int32_t *part);
+
+/* Overlap maps of subdomain p. omega/owned/iface need room for n entries. */
+int or_overlap(int n, const int32_t *rp, const int32_t *ci, const int32_t *part, int P, int p,
+               int gamma, int32_t *omega, int32_t *n_omega, uint8_t *owned, int32_t *iface,
+               int32_t *n_iface);
+
+/* Banded Cholesky. band[i*(w+1)+t] holds A[i][i-w+t] (t = 0..w); in place -> L. */
+int or_band_cholesky(int n, int w, double *band);
+/* Solve L L^T x = rhs in place (FP64). */
+void or_band_solve(int n, int w, const double *L, double *x);
+/* Same with factors rounded to `prec` (OR_FP32 / OR_BF16) and FP32 arithmetic. */
+void or_band_solve_lowp(int n, int w, const double *L, int prec, double *x);
+
+/* Dense LU with partial pivoting: solves A x = b in place (A overwritten). */
+int or_dense_lu_solve(int n, double *A, double *b);
+
+/* m iterations of textbook CG on A d = rhs from d = 0 (FP64 or FP32 arithmetic). */
+void or_cg(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *rhs,
+           int m, int prec, double *d);
+/* ILU(0) on the CSR pattern (IKJ order). lu has the pattern of A. */
+int or_ilu0(int n, const int32_t *rp, const int32_t *ci, const double *val, double *lu);
+/* m iterations of CG preconditioned by the ILU(0) factors, from d = 0. */
+void or_pcg_ilu0(int n, const int32_t *rp, const int32_t *ci, const double *val,
+                 const double *lu, const double *rhs, int m, int prec, double *d);
+
+/* r = b - A x; returns ||r||_2^2 summed in index order. r may be NULL. */
+double or_residual(int n, const int32_t *rp, const int32_t *ci, const double *val,
+                   const double *b, const double *x, double *r);
+
+/*
+ * Synchronous RAS in correction form (Algorithm 1 with the RAS update of
+ * Sec. 2.1). x holds x^0 on entry and the final iterate on exit. hist (may be
+ * NULL) receives ||b - A x^k|| / ||b|| for k = 0..iters. nthreads > 1 runs the
+ * independent local solves of one iteration in parallel (same result).
+ */
+int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *b,
+                const int32_t *part, int P, int gamma, int kind, int prec, int m, double tol,
+                int max_iter, int nthreads, double *x, double *hist, int32_t *iters);
+
+#endif
