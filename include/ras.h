@@ -1,0 +1,183 @@
+/*
+ * ras.h - C ABI of the GB300 asynchronous Restricted Additive Schwarz solver.
+ *
+ * The library solves A x = b (Eq. 1) for a sparse symmetric positive definite
+ * A by Restricted Additive Schwarz (Sec. 2.1): the unknowns are partitioned
+ * into subdomains (Sec. 3.2.1), each subdomain is grown by `overlap` layers of
+ * graph neighbours (Fig. 1), every subdomain solves its local problem on the
+ * overlapped set and keeps only the values it owns. Subdomains run as CTAs of
+ * one persistent kernel on one GPU. In RAS_SYNC mode iterations are separated
+ * by a grid-wide barrier (the synchronous solver of Sec. 2.1 / Sec. 3.4); in
+ * RAS_ASYNC mode every CTA publishes its owned values with release stores and
+ * reads its neighbours' values with acquire loads whenever it is ready, with
+ * no barrier (the asynchronous solver of Sec. 2.1 / Sec. 3.4). Convergence
+ * uses the local criterion of Eq. 2 and the global criterion ||r|| < tol ||b||
+ * verified after termination (Sec. 3.3.2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a ras_status. Errors are returned, never raised or
+ *    aborted. Pointers marked HOST are read on the CPU; DEVICE pointers must
+ *    be CUDA device memory of the current device.
+ *  - The caller owns every input buffer; the library deep-copies what it
+ *    keeps, so inputs may be freed as soon as a call returns.
+ *  - Work is issued on the stream given to ras_setup (NULL = legacy default
+ *    stream). Calls that return results to the host synchronise that stream
+ *    before returning.
+ *  - A context must not be used by two host threads at the same time.
+ */
+#ifndef RAS_H
+#define RAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ras_ctx ras_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  RAS_OK = 0,
+  RAS_EINVAL = 1,   /* invalid argument (sizes, indices, pointers, options) */
+  RAS_ENOMEM = 2,   /* host or device allocation failed */
+  RAS_ENOTSPD = 3,  /* a local factorisation met a non-positive pivot */
+  RAS_ENOCONV = 4,  /* max updates / restarts reached; x holds the last iterate */
+  RAS_ETIMEOUT = 5, /* a device-side wait exceeded its limit; x is undefined */
+  RAS_ECUDA = 6,    /* a CUDA runtime call failed */
+  RAS_ENOTSUP = 7   /* valid but unsupported (e.g. local bandwidth too large) */
+} ras_status;
+
+typedef enum { RAS_SYNC = 0, RAS_ASYNC = 1 } ras_mode;
+
+/* Local solvers (Sec. 3.3.1): a banded Cholesky factorisation computed once
+ * in ras_setup with triangular solves in every update, or `inner_iters` steps
+ * of CG / ILU(0)-preconditioned CG from a zero initial guess. */
+typedef enum { RAS_LOCAL_BANDCHOL = 0, RAS_LOCAL_CG = 1, RAS_LOCAL_ILU0_CG = 2 } ras_local_kind;
+
+/* Precision of the local solve. The outer residual, the update of x and the
+ * convergence tests are always FP64. RAS_FP32: factors / local matrix stored
+ * and used in FP32. RAS_BF16_STORE: band factors stored in bfloat16, applied
+ * in FP32 arithmetic (RAS_LOCAL_BANDCHOL only). */
+typedef enum { RAS_FP64 = 0, RAS_FP32 = 1, RAS_BF16_STORE = 2 } ras_prec;
+
+/* Sparse matrix in CSR form. HOST pointers. row_ptr[n+1] (row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz), col_idx[nnz] in [0, n) and strictly
+ * ascending within each row, val[nnz]. The pattern must be structurally
+ * symmetric and every row must hold its diagonal. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const double *val;
+} ras_csr;
+
+typedef struct {
+  int32_t kind;        /* ras_local_kind */
+  int32_t prec;        /* ras_prec */
+  int32_t inner_iters; /* CG / PCG steps per local solve (ignored for BANDCHOL) */
+} ras_local_solver;
+
+/* Result of one solve. */
+typedef struct {
+  int64_t iterations;     /* sync: RAS iterations k of the returned x^k;
+                             async: median number of local updates */
+  int64_t updates_min;    /* per-subdomain local-solve counts */
+  int64_t updates_median;
+  int64_t updates_max;
+  double relres;          /* ||b - A x|| / ||b|| of the returned x, FP64, on device */
+  double solve_ms;        /* device time of the solve (CUDA events) */
+  int32_t restarts;       /* async: post-termination checks that failed */
+  int32_t status;         /* same as the return value of the solve */
+} ras_solve_info;
+
+/* ------------------------------------------------------------------------ */
+/* Partitioners (Sec. 3.2.1). HOST memory, no GPU work.                      */
+/* ------------------------------------------------------------------------ */
+
+/* regular2d partition of an nx x ny grid (index y*nx + x): block column
+ * floor(x*px/nx), block row floor(y*py/ny), part = row*px + column.
+ * regular1d is px = 1. part[nx*ny] is written. */
+ras_status ras_partition_regular2d(int32_t nx, int32_t ny, int32_t px, int32_t py,
+                                   int32_t *part);
+
+/* Seeded BFS-growth graph partition into num_parts parts (the stand-in for
+ * the Metis partitioner of Sec. 3.2.1): random target sizes within +-30% of
+ * n/num_parts, random seed vertices, round-robin breadth-first growth, and
+ * leftover vertices joined to their smallest neighbouring part. Deterministic
+ * for a given seed; bit-identical to the published rule on any host.
+ * part[A->n] is written. */
+ras_status ras_partition_bfs(const ras_csr *A, int32_t num_parts, uint64_t seed, int32_t *part);
+
+/* ------------------------------------------------------------------------ */
+/* Setup, solve, teardown (Algorithm 1: initialization_and_setup / solve).   */
+/* ------------------------------------------------------------------------ */
+
+/* Builds the overlapped subdomains Omega_p (O_p plus `overlap` graph layers,
+ * Fig. 1), their restriction maps and local matrices (Sec. 3.2.2), factorises
+ * the local matrices on the GPU (banded Cholesky in FP64, stored in the
+ * requested precision) or the ILU(0) preconditioners, and uploads everything.
+ * partition: HOST int32[A->n] with values in [0, num_parts), every part
+ * non-empty. cuda_stream: a cudaStream_t or NULL. On failure *out = NULL.
+ * Setup is not part of the solve timing (Sec. 3.1). */
+ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t num_parts,
+                     int32_t overlap, const ras_local_solver *local_solver, void *cuda_stream,
+                     ras_ctx **out);
+
+/* Solves A x = b. b: DEVICE double[n]; x: DEVICE double[n], holds the initial
+ * guess on entry and the solution on return. tol: relative residual target
+ * (global criterion ||b - A x|| < tol ||b||, Sec. 3.3.2). mode: ras_mode.
+ * max_updates: limit on local updates per subdomain (<= 0: 10^6).
+ * info may be NULL. Synchronises the context's stream. RAS_ENOCONV leaves
+ * the last iterate in x. */
+ras_status ras_solve(ras_ctx *ctx, const double *b, double *x, double tol, int32_t mode,
+                     int64_t max_updates, ras_solve_info *info);
+
+/* Same as ras_solve with HOST b and x: copies b and x to the device, solves,
+ * and copies x back, all on the context's stream. Pinned host memory gives
+ * asynchronous copies; pageable memory works but is slower. */
+ras_status ras_solve_host(ras_ctx *ctx, const double *b_host, double *x_host, double tol,
+                          int32_t mode, int64_t max_updates, ras_solve_info *info);
+
+/* Solves several independent systems in ONE persistent launch. All contexts
+ * must share the local solver kind and precision and the stream of ctxs[0]
+ * is used. b[i], x[i]: DEVICE arrays of ctxs[i]'s size. infos: num entries
+ * or NULL. Returns the first non-OK status. */
+ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *const *b,
+                           double *const *x, double tol, int32_t mode, int64_t max_updates,
+                           ras_solve_info *infos);
+
+/* Releases a context (NULL is allowed). Synchronises its stream first. */
+ras_status ras_destroy(ras_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Inspection (tests, tools)                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Maps of subdomain p, as built by ras_setup. Returned pointers are HOST
+ * memory owned by the context and valid until ras_destroy:
+ * omega[n_omega] (global ids of Omega_p, ascending), owned_mask[n_omega]
+ * (1 where omega[t] is in O_p), iface[n_iface] (E_p: points outside Omega_p
+ * coupled to it, ascending). */
+ras_status ras_get_maps(const ras_ctx *ctx, int32_t p, const int32_t **omega, int32_t *n_omega,
+                        const uint8_t **owned_mask, const int32_t **iface, int32_t *n_iface);
+
+/* Sizes of the context: number of subdomains, global n, maximum local
+ * half-bandwidth, and the bytes of device memory it holds. */
+ras_status ras_get_info(const ras_ctx *ctx, int32_t *num_parts, int32_t *n, int32_t *max_bandwidth,
+                        int64_t *device_bytes);
+
+/* Per-subdomain local-update counts of the last solve: counts[num_parts]. */
+ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
+
+/* FP64 global relative residual ||b - A x|| / ||b|| computed on the device
+ * (b, x DEVICE). Synchronises the context's stream. */
+ras_status ras_relres(ras_ctx *ctx, const double *b, const double *x, double *relres);
+
+/* Static description of a status code. */
+const char *ras_status_str(ras_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAS_H */

@@ -1,0 +1,1144 @@
+// Host side of the GB300 RAS solver: the C ABI of include/ras.h.
+//
+//   * partitioners (Sec. 3.2.1): regular2d and the seeded BFS-growth graph
+//     partitioner that stands in for Metis;
+//   * the overlap / restriction-map builder (Sec. 2.1, Fig. 1; Sec. 3.2.2):
+//     Omega_p = O_p grown by `overlap` layers of graph neighbours, the
+//     external interface E_p, the local matrix A_p and the residual operator
+//     of Omega_p's rows;
+//   * local-solver setup (Sec. 3.3.1): banded Cholesky on the GPU, or ILU(0)
+//     factors and level schedules for the preconditioned CG;
+//   * launch planning (CTA count from occupancy, longest-processing-time
+//     assignment of subdomains to CTAs) and the solve / batch-solve drivers
+//     (Algorithm 1's solve loop runs inside one cooperative launch).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <queue>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ras.h"
+#include "ras_internal.h"
+#include "ras_launch.h"
+
+using namespace ras;
+
+namespace {
+
+// ---------------------------------------------------------------- utilities
+
+int host_threads() {
+  unsigned h = std::thread::hardware_concurrency();
+  if (h == 0) h = 4;
+  return (int)std::min(16u, h);
+}
+
+// Runs f(p) for p in [0, n) on a few host threads.
+void parallel_for(int n, const std::function<void(int)> &f) {
+  const int nt = std::min(host_threads(), std::max(n, 1));
+  if (nt <= 1) {
+    for (int p = 0; p < n; ++p) f(p);
+    return;
+  }
+  std::atomic<int> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&]() {
+      for (int p; (p = next.fetch_add(1)) < n;) f(p);
+    });
+  for (auto &t : th) t.join();
+}
+
+uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  // SplitMix64 (Steele, Lea & Flood 2014): state advanced k+1 times by the
+  // golden-ratio increment, then the variant-13 finaliser.
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double unit_double(uint64_t z) { return (double)(z >> 11) * 0x1.0p-53; }
+
+ras_status check_csr(const ras_csr *A) {
+  if (!A || A->n <= 0 || !A->row_ptr || !A->col_idx || !A->val) return RAS_EINVAL;
+  const int n = A->n;
+  if (A->row_ptr[0] != 0 || (int64_t)A->row_ptr[n] != A->nnz) return RAS_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const int a = A->row_ptr[i], b = A->row_ptr[i + 1];
+    if (b < a) return RAS_EINVAL;
+    bool diag = false;
+    for (int k = a; k < b; ++k) {
+      const int c = A->col_idx[k];
+      if (c < 0 || c >= n) return RAS_EINVAL;
+      if (k > a && c <= A->col_idx[k - 1]) return RAS_EINVAL;
+      if (c == i) diag = true;
+      if (!std::isfinite(A->val[k])) return RAS_EINVAL;
+    }
+    if (!diag) return RAS_EINVAL;
+  }
+  // structural symmetry: (i, c) present => (c, i) present
+  for (int i = 0; i < n; ++i)
+    for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) {
+      const int c = A->col_idx[k];
+      const int32_t *b = A->col_idx + A->row_ptr[c], *e = A->col_idx + A->row_ptr[c + 1];
+      if (!std::binary_search(b, e, i)) return RAS_EINVAL;
+    }
+  return RAS_OK;
+}
+
+#define CUDA_TRY(expr)                                 \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) {                           \
+      last_cuda_error() = e_;                          \
+      return e_ == cudaErrorMemoryAllocation ? RAS_ENOMEM : RAS_ECUDA; \
+    }                                                  \
+  } while (0)
+
+cudaError_t &last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+int64_t env_int(const char *name, int64_t dflt) {
+  const char *v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  return std::strtoll(v, nullptr, 10);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- context
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct LaunchPlan {
+  int nt = 0, grid = 0;
+  size_t smem = 0;
+  int Wmax = 0, npad_max = 0;
+  std::vector<Item> items;
+  std::vector<int32_t> cta_off, cta_sys, cta_sys_off;
+  // device copies
+  Item *d_items = nullptr;
+  int32_t *d_cta_off = nullptr, *d_cta_sys = nullptr, *d_cta_sys_off = nullptr;
+  void release() {
+    cudaFree(d_items);
+    cudaFree(d_cta_off);
+    cudaFree(d_cta_sys);
+    cudaFree(d_cta_sys_off);
+    d_items = nullptr;
+    d_cta_off = d_cta_sys = d_cta_sys_off = nullptr;
+  }
+};
+
+struct ras_ctx {
+  cudaStream_t stream = nullptr;
+  int n = 0, P = 0, K = 0, overlap = 0;
+  ras_local_solver ls{};
+  int maxw = 0;  // largest true local half-bandwidth
+  // host copies of the maps (inspection)
+  std::vector<std::vector<int32_t>> omega, iface;
+  std::vector<std::vector<uint8_t>> owned;
+  std::vector<SubDesc> subs;
+  std::vector<double> cost;  // per-subdomain work estimate for the launch plan
+  // device data
+  std::vector<DevBuf> bufs;
+  SubDesc *d_subs = nullptr;
+  SubState *d_sub = nullptr;
+  SysState *d_st = nullptr;
+  int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
+          *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
+  uint8_t *d_ownf = nullptr;
+  double *d_rval = nullptr, *d_xalt = nullptr;
+  void *d_fac = nullptr, *d_lval = nullptr, *d_lu = nullptr;
+  int64_t device_bytes = 0;
+  // launch state
+  LaunchPlan plan;
+  SysDesc *d_sysdesc = nullptr;
+  GridCtl *d_ctl = nullptr;
+  SysDesc *h_sysdesc = nullptr;  // pinned staging
+  GridCtl *h_ctl = nullptr;
+  SysState *h_st = nullptr;
+  SubState *h_sub = nullptr;
+  double *d_bx = nullptr;  // device b and x for ras_solve_host
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<int64_t> last_updates;
+
+  template <typename T>
+  ras_status alloc(T *&ptr, size_t count) {
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      last_cuda_error() = e;
+      return RAS_ENOMEM;
+    }
+    bufs.push_back({p, bytes});
+    device_bytes += (int64_t)bytes;
+    ptr = static_cast<T *>(p);
+    return RAS_OK;
+  }
+  template <typename T>
+  ras_status upload(T *&ptr, const std::vector<T> &v) {
+    ras_status s = alloc(ptr, v.size());
+    if (s != RAS_OK) return s;
+    if (!v.empty()) {
+      cudaError_t e = cudaMemcpyAsync(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                      stream);
+      if (e != cudaSuccess) {
+        last_cuda_error() = e;
+        return RAS_ECUDA;
+      }
+    }
+    return RAS_OK;
+  }
+  ~ras_ctx() {
+    cudaStreamSynchronize(stream);
+    plan.release();
+    for (auto &b : bufs) cudaFree(b.p);
+    cudaFreeHost(h_sysdesc);
+    cudaFreeHost(h_ctl);
+    cudaFreeHost(h_st);
+    cudaFreeHost(h_sub);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+};
+
+namespace {
+
+size_t prec_bytes(int prec) { return prec == RAS_FP64 ? 8 : prec == RAS_FP32 ? 4 : 2; }
+
+// Write value v in the storage precision at dst[k].
+void store_prec(void *dst, size_t k, int prec, double v) {
+  if (prec == RAS_FP64) {
+    static_cast<double *>(dst)[k] = v;
+  } else if (prec == RAS_FP32) {
+    static_cast<float *>(dst)[k] = (float)v;
+  } else {
+    // bfloat16, round to nearest even from the float32 value
+    float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    static_cast<uint16_t *>(dst)[k] = (uint16_t)(u >> 16);
+  }
+}
+
+// Per-subdomain maps built on the host.
+struct SubMaps {
+  std::vector<int32_t> omega;   // ascending global ids
+  std::vector<uint8_t> owned;
+  std::vector<int32_t> iface;   // ascending
+  std::vector<int32_t> nbr;     // neighbouring subdomains (ascending, != p)
+  int w = 0;                    // half-bandwidth of A_p in local order
+};
+
+// Omega_p by breadth-first layers from O_p over the graph of A (Fig. 1: one
+// layer per unit of overlap); E_p = points outside Omega_p adjacent to it.
+void build_maps(const ras_csr *A, const int32_t *part, const std::vector<int32_t> &owned_list,
+                int p, int overlap, std::vector<int32_t> &mark, SubMaps &m) {
+  const int tag = 2 * p + 1;  // mark[] == tag: in Omega_p; == tag+1: in E_p
+  std::vector<int32_t> frontier(owned_list), next, all(owned_list);
+  for (int v : owned_list) mark[v] = tag;
+  for (int layer = 0; layer < overlap; ++layer) {
+    next.clear();
+    for (int v : frontier)
+      for (int k = A->row_ptr[v]; k < A->row_ptr[v + 1]; ++k) {
+        const int c = A->col_idx[k];
+        if (mark[c] != tag) {
+          mark[c] = tag;
+          next.push_back(c);
+        }
+      }
+    all.insert(all.end(), next.begin(), next.end());
+    frontier.swap(next);
+  }
+  std::sort(all.begin(), all.end());
+  m.omega = all;
+  m.owned.resize(all.size());
+  for (size_t t = 0; t < all.size(); ++t) m.owned[t] = part[all[t]] == p ? 1 : 0;
+  m.iface.clear();
+  for (int v : all)
+    for (int k = A->row_ptr[v]; k < A->row_ptr[v + 1]; ++k) {
+      const int c = A->col_idx[k];
+      if (mark[c] != tag && mark[c] != tag + 1) {
+        mark[c] = tag + 1;
+        m.iface.push_back(c);
+      }
+    }
+  std::sort(m.iface.begin(), m.iface.end());
+  std::vector<int32_t> nb;
+  for (int v : all)
+    if (part[v] != p) nb.push_back(part[v]);
+  for (int v : m.iface) nb.push_back(part[v]);
+  std::sort(nb.begin(), nb.end());
+  nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+  m.nbr = nb;
+  // half-bandwidth in local (ascending global) order
+  int w = 0;
+  for (size_t i = 0; i < all.size(); ++i) {
+    const int g = all[i];
+    for (int k = A->row_ptr[g]; k < A->row_ptr[g + 1]; ++k) {
+      auto it = std::lower_bound(all.begin(), all.end(), A->col_idx[k]);
+      if (it != all.end() && *it == A->col_idx[k]) w = std::max(w, std::abs((int)(it - all.begin()) - (int)i));
+    }
+  }
+  m.w = w;
+}
+
+inline int local_index(const std::vector<int32_t> &omega, int g) {
+  auto it = std::lower_bound(omega.begin(), omega.end(), g);
+  return (it != omega.end() && *it == g) ? (int)(it - omega.begin()) : -1;
+}
+
+// ILU(0) of a local CSR matrix (FP64), row by row: for each k < i in row i,
+// l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj for every j > k of row k that is
+// also in row i (positions found through a scatter map of row i).
+bool ilu0_local(int n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                std::vector<double> &a) {
+  std::vector<int32_t> pos(n, -1), diag(n, -1);
+  for (int i = 0; i < n; ++i)
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] == i) diag[i] = k;
+  for (int i = 0; i < n; ++i) {
+    for (int k = rp[i]; k < rp[i + 1]; ++k) pos[ci[k]] = k;
+    for (int kk = rp[i]; kk < rp[i + 1]; ++kk) {
+      const int k = ci[kk];
+      if (k >= i) break;
+      const double ukk = a[diag[k]];
+      if (ukk == 0.0) return false;
+      const double lik = a[kk] / ukk;
+      a[kk] = lik;
+      for (int jj = diag[k] + 1; jj < rp[k + 1]; ++jj) {
+        const int q = pos[ci[jj]];
+        if (q >= 0) a[q] -= lik * a[jj];
+      }
+    }
+    for (int k = rp[i]; k < rp[i + 1]; ++k) pos[ci[k]] = -1;
+    if (!(a[diag[i]] > 0.0)) return false;
+  }
+  return true;
+}
+
+// Level sets of the unit-lower (forward) and upper (backward) triangular
+// solves: level(i) = 1 + max level of the rows it depends on.
+void level_schedule(int n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                    std::vector<int32_t> &ptr_f, std::vector<int32_t> &rows_f,
+                    std::vector<int32_t> &ptr_b, std::vector<int32_t> &rows_b) {
+  std::vector<int32_t> lev(n, 0);
+  auto bucket = [&](std::vector<int32_t> &ptr, std::vector<int32_t> &rows) {
+    const int nl = n ? *std::max_element(lev.begin(), lev.end()) + 1 : 0;
+    ptr.assign(nl + 1, 0);
+    for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+    for (int l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    rows.assign(n, 0);
+    for (int i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;
+  };
+  for (int i = 0; i < n; ++i) {
+    int l = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] < i) l = std::max(l, lev[ci[k]] + 1);
+    lev[i] = l;
+  }
+  bucket(ptr_f, rows_f);
+  for (int i = n - 1; i >= 0; --i) {
+    int l = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] > i) l = std::max(l, lev[ci[k]] + 1);
+    lev[i] = l;
+  }
+  bucket(ptr_b, rows_b);
+}
+
+// Longest-processing-time assignment of items to `grid` CTAs.
+void assign_items(LaunchPlan &pl, const std::vector<Item> &items, const std::vector<double> &cost,
+                  int grid) {
+  const int ni = (int)items.size();
+  std::vector<int> order(ni);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> per(grid);
+  std::vector<std::vector<int>> sys_of(grid);
+  using E = std::pair<double, int>;
+  std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
+  for (int c = 0; c < grid; ++c) pq.push({0.0, c});
+  std::vector<E> held;
+  for (int idx : order) {
+    const int s = items[idx].sys;
+    // least-loaded CTA that can still take this item's system
+    held.clear();
+    int chosen = -1;
+    while (!pq.empty()) {
+      E e = pq.top();
+      pq.pop();
+      auto &ss = sys_of[e.second];
+      if ((int)ss.size() < kMaxCtaSys || std::find(ss.begin(), ss.end(), s) != ss.end()) {
+        chosen = e.second;
+        per[chosen].push_back(idx);
+        if (std::find(ss.begin(), ss.end(), s) == ss.end()) ss.push_back(s);
+        pq.push({e.first + cost[idx], chosen});
+        break;
+      }
+      held.push_back(e);
+    }
+    for (auto &e : held) pq.push(e);
+    if (chosen < 0) {  // cannot happen while grid * kMaxCtaSys >= systems
+      per[0].push_back(idx);
+    }
+  }
+  pl.items.clear();
+  pl.cta_off.assign(1, 0);
+  pl.cta_sys.clear();
+  pl.cta_sys_off.assign(1, 0);
+  for (int c = 0; c < grid; ++c) {
+    auto &v = per[c];
+    std::sort(v.begin(), v.end(), [&](int a, int b) {
+      return items[a].sys != items[b].sys ? items[a].sys < items[b].sys : items[a].p < items[b].p;
+    });
+    std::vector<int> sl;
+    for (int idx : v) {
+      Item it = items[idx];
+      auto f = std::find(sl.begin(), sl.end(), it.sys);
+      if (f == sl.end()) {
+        sl.push_back(it.sys);
+        f = sl.end() - 1;
+      }
+      it.ls = (int)(f - sl.begin());
+      pl.items.push_back(it);
+    }
+    for (int s : sl) {
+      bool lead = false;
+      for (int idx : v)
+        if (items[idx].sys == s && items[idx].p == 0) lead = true;
+      pl.cta_sys.push_back(s);
+      pl.cta_sys.push_back(lead ? 1 : 0);
+    }
+    pl.cta_off.push_back((int32_t)pl.items.size());
+    pl.cta_sys_off.push_back((int32_t)(pl.cta_sys.size() / 2));
+  }
+}
+
+ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Item> &items,
+                       const std::vector<double> &cost, int Wmax, int npad_max,
+                       cudaStream_t stream) {
+  pl.release();
+  int dev = 0, nsm = 0, max_smem = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int nt_pref = (int)env_int("RAS_CTA_THREADS", 256);
+  pl.nt = main_threads(kind, nt_pref);
+  pl.Wmax = Wmax;
+  pl.npad_max = npad_max;
+  pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max);
+  if (pl.smem + 4096 > (size_t)max_smem) return RAS_ENOTSUP;
+  const int occ = main_occupancy(kind, prec, pl.nt, pl.smem);
+  if (occ <= 0) return RAS_ENOTSUP;
+  int64_t cap = (int64_t)occ * nsm;
+  const int64_t lim = env_int("RAS_MAX_CTAS", 0);
+  if (lim > 0) cap = std::min<int64_t>(cap, lim);
+  pl.grid = (int)std::min<int64_t>((int64_t)items.size(), cap);
+  if (pl.grid <= 0) return RAS_EINVAL;
+  assign_items(pl, items, cost, pl.grid);
+  auto up = [&](auto *&d, const auto &v) -> cudaError_t {
+    using T = typename std::remove_reference<decltype(v)>::type::value_type;
+    cudaError_t e = cudaMalloc((void **)&d, std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream);
+  };
+  CUDA_TRY(up(pl.d_items, pl.items));
+  CUDA_TRY(up(pl.d_cta_off, pl.cta_off));
+  CUDA_TRY(up(pl.d_cta_sys, pl.cta_sys));
+  CUDA_TRY(up(pl.d_cta_sys_off, pl.cta_sys_off));
+  return RAS_OK;
+}
+
+SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
+  SysDesc s{};
+  s.b = b;
+  s.x = x;
+  s.xalt = c->d_xalt;
+  s.n = c->n;
+  s.P = c->P;
+  s.K = c->K;
+  s.tol2 = tol * tol;
+  s.subs = c->d_subs;
+  s.sub = c->d_sub;
+  s.st = c->d_st;
+  s.gidx = c->d_gidx;
+  s.ownf = c->d_ownf;
+  s.rcol = c->d_rcol;
+  s.rval = c->d_rval;
+  s.own_l = c->d_own;
+  s.fac = c->d_fac;
+  s.lcol = c->d_lcol;
+  s.lval = c->d_lval;
+  s.luval = c->d_lu;
+  s.lev_ptr = c->d_levp;
+  s.lev_rows = c->d_levr;
+  s.nbr = c->d_nbr;
+  return s;
+}
+
+int64_t timeout_ns() { return env_int("RAS_TIMEOUT_MS", 20000) * 1000000ll; }
+
+}  // namespace
+
+// ========================================================================
+// C ABI
+// ========================================================================
+
+extern "C" {
+
+const char *ras_status_str(ras_status s) {
+  switch (s) {
+    case RAS_OK: return "ok";
+    case RAS_EINVAL: return "invalid argument";
+    case RAS_ENOMEM: return "out of memory";
+    case RAS_ENOTSPD: return "local matrix not positive definite";
+    case RAS_ENOCONV: return "no convergence within the update limit";
+    case RAS_ETIMEOUT: return "device-side wait timed out";
+    case RAS_ECUDA: return "CUDA runtime error";
+    case RAS_ENOTSUP: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+ras_status ras_partition_regular2d(int32_t nx, int32_t ny, int32_t px, int32_t py, int32_t *part) {
+  if (!part || nx <= 0 || ny <= 0 || px <= 0 || py <= 0 || px > nx || py > ny) return RAS_EINVAL;
+  for (int32_t y = 0; y < ny; ++y) {
+    const int32_t by = (int32_t)(((int64_t)y * py) / ny);
+    for (int32_t x = 0; x < nx; ++x)
+      part[(int64_t)y * nx + x] = by * px + (int32_t)(((int64_t)x * px) / nx);
+  }
+  return RAS_OK;
+}
+
+ras_status ras_partition_bfs(const ras_csr *A, int32_t P, uint64_t seed, int32_t *part) {
+  if (!A || !part || A->n <= 0 || P <= 0 || P > A->n || !A->row_ptr || !A->col_idx) return RAS_EINVAL;
+  const int n = A->n;
+  // target sizes from random weights in [0.7, 1.3]
+  std::vector<double> wgt(P);
+  double wsum = 0.0;
+  for (int p = 0; p < P; ++p) {
+    wgt[p] = 1.0 + 0.3 * (2.0 * unit_double(splitmix64_at(seed, (uint64_t)p)) - 1.0);
+    wsum += wgt[p];
+  }
+  std::vector<int64_t> target(P), size(P, 0);
+  int64_t tsum = 0;
+  for (int p = 0; p < P; ++p) {
+    target[p] = (int64_t)std::floor((double)n * wgt[p] / wsum);
+    tsum += target[p];
+  }
+  for (int64_t rem = n - tsum, p = 0; rem != 0; p = (p + 1) % P) {
+    if (rem > 0) { ++target[p]; --rem; }
+    else if (target[p] > 0) { --target[p]; ++rem; }
+  }
+  std::fill(part, part + n, -1);
+  std::vector<std::vector<int32_t>> queue(P);
+  std::vector<size_t> qhead(P, 0);
+  std::vector<int32_t> cursor(A->row_ptr, A->row_ptr + n);
+  for (int p = 0; p < P; ++p) {
+    int64_t v = (int64_t)std::floor(unit_double(splitmix64_at(seed, (uint64_t)(P + p))) * (double)n);
+    if (v >= n) v = n - 1;
+    while (part[v] != -1) v = (v + 1) % n;
+    part[v] = p;
+    size[p] = 1;
+    queue[p].push_back((int32_t)v);
+  }
+  for (bool grew = true; grew;) {
+    grew = false;
+    for (int p = 0; p < P; ++p) {
+      if (size[p] >= target[p]) continue;
+      while (qhead[p] < queue[p].size()) {
+        const int f = queue[p][qhead[p]];
+        int got = -1;
+        while (cursor[f] < A->row_ptr[f + 1]) {
+          const int c = A->col_idx[cursor[f]++];
+          if (part[c] == -1) { got = c; break; }
+        }
+        if (got < 0) { ++qhead[p]; continue; }
+        part[got] = p;
+        ++size[p];
+        queue[p].push_back(got);
+        grew = true;
+        break;
+      }
+    }
+  }
+  for (;;) {
+    for (bool changed = true; changed;) {
+      changed = false;
+      for (int i = 0; i < n; ++i) {
+        if (part[i] != -1) continue;
+        int best = -1;
+        for (int k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) {
+          const int q = part[A->col_idx[k]];
+          if (q >= 0 && (best < 0 || size[q] < size[best] || (size[q] == size[best] && q < best)))
+            best = q;
+        }
+        if (best >= 0) {
+          part[i] = best;
+          ++size[best];
+          changed = true;
+        }
+      }
+    }
+    const int32_t *first = std::find(part, part + n, -1);
+    if (first == part + n) break;
+    const int q = (int)(std::min_element(size.begin(), size.end()) - size.begin());
+    part[first - part] = q;
+    ++size[q];
+  }
+  return RAS_OK;
+}
+
+ras_status ras_destroy(ras_ctx *ctx) {
+  delete ctx;
+  return RAS_OK;
+}
+
+ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int32_t overlap,
+                     const ras_local_solver *lsv, void *cuda_stream, ras_ctx **out) {
+  if (!out) return RAS_EINVAL;
+  *out = nullptr;
+  if (!partition || P <= 0 || overlap < 0 || !lsv) return RAS_EINVAL;
+  if (lsv->kind < RAS_LOCAL_BANDCHOL || lsv->kind > RAS_LOCAL_ILU0_CG) return RAS_EINVAL;
+  if (lsv->prec < RAS_FP64 || lsv->prec > RAS_BF16_STORE) return RAS_EINVAL;
+  if (lsv->prec == RAS_BF16_STORE && lsv->kind != RAS_LOCAL_BANDCHOL) return RAS_EINVAL;
+  if (lsv->kind != RAS_LOCAL_BANDCHOL && lsv->inner_iters <= 0) return RAS_EINVAL;
+  ras_status st = check_csr(A);
+  if (st != RAS_OK) return st;
+  const int n = A->n;
+  std::vector<std::vector<int32_t>> owned_lists(P);
+  for (int i = 0; i < n; ++i) {
+    if (partition[i] < 0 || partition[i] >= P) return RAS_EINVAL;
+    owned_lists[partition[i]].push_back(i);
+  }
+  for (int p = 0; p < P; ++p)
+    if (owned_lists[p].empty()) return RAS_EINVAL;
+
+  std::unique_ptr<ras_ctx> c(new ras_ctx());
+  c->stream = (cudaStream_t)cuda_stream;
+  c->n = n;
+  c->P = P;
+  c->overlap = overlap;
+  c->ls = *lsv;
+  int K = 0;
+  for (int i = 0; i < n; ++i) K = std::max(K, A->row_ptr[i + 1] - A->row_ptr[i]);
+  c->K = K;
+  const int kind = lsv->kind, prec = lsv->prec;
+
+  // ---- maps (parallel over subdomains; each worker has its own mark array)
+  std::vector<SubMaps> maps(P);
+  {
+    const int nt = std::min(host_threads(), P);
+    std::vector<std::vector<int32_t>> marks(nt, std::vector<int32_t>(n, -1));
+    std::atomic<int> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&, t]() {
+        for (int p; (p = next.fetch_add(1)) < P;)
+          build_maps(A, partition, owned_lists[p], p, overlap, marks[t], maps[p]);
+      });
+    for (auto &t : th) t.join();
+  }
+
+  // ---- descriptors and offsets
+  c->subs.resize(P);
+  c->cost.resize(P);
+  int64_t rows = 0, owns = 0, fac = 0, levp = 0, levr = 0;
+  int nbrs = 0, Wmax = 0, npad_max = 0;
+  const int m = std::max(lsv->inner_iters, 1);
+  for (int p = 0; p < P; ++p) {
+    SubDesc &d = c->subs[p];
+    const SubMaps &mp = maps[p];
+    d.n = (int32_t)mp.omega.size();
+    d.npad = (d.n + 31) / 32 * 32;
+    d.n_own = (int32_t)owned_lists[p].size();
+    d.W = std::max(mp.w, 31);
+    d.row_off = rows;
+    d.own_off = owns;
+    d.fac_off = fac;
+    d.nbr_off = nbrs;
+    d.n_nbr = (int32_t)mp.nbr.size();
+    rows += d.npad;
+    owns += d.n_own;
+    nbrs += d.n_nbr;
+    if (kind == RAS_LOCAL_BANDCHOL) {
+      if (mp.w > 160) return RAS_ENOTSUP;
+      fac += 2ll * (d.npad / 32) * (d.W + 1) * 32;
+      Wmax = std::max(Wmax, d.W);
+      c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
+    } else {
+      c->cost[p] = (double)d.n * K * (m + 1) * (kind == RAS_LOCAL_ILU0_CG ? 3.0 : 1.0);
+    }
+    c->maxw = std::max(c->maxw, mp.w);
+    npad_max = std::max(npad_max, d.npad);
+  }
+  c->plan.Wmax = kind == RAS_LOCAL_BANDCHOL ? Wmax : 0;
+  c->plan.npad_max = npad_max;
+
+  // ---- per-row host arrays
+  std::vector<int32_t> gidx(rows, 0), rcol(rows * K, 0), own(owns), nbr(nbrs);
+  std::vector<uint8_t> ownf(rows, 0);
+  std::vector<double> rval(rows * K, 0.0);
+  std::vector<int32_t> lcol;
+  std::vector<double> lval64, lu64;
+  std::vector<double> band;  // FP64 bands for the GPU factorisation
+  std::vector<int64_t> band_off(P, 0);
+  if (kind != RAS_LOCAL_BANDCHOL) {
+    lcol.assign(rows * K, 0);
+    lval64.assign(rows * K, 0.0);
+    if (kind == RAS_LOCAL_ILU0_CG) lu64.assign(rows * K, 0.0);
+  } else {
+    int64_t bsz = 0;
+    for (int p = 0; p < P; ++p) {
+      band_off[p] = bsz;
+      bsz += (int64_t)c->subs[p].n * (maps[p].w + 1);
+    }
+    band.assign(bsz, 0.0);
+  }
+  std::vector<std::vector<int32_t>> lev_ptr(P), lev_rows(P);
+  std::atomic<int> ilu_fail(0);
+  parallel_for(P, [&](int p) {
+    const SubDesc &d = c->subs[p];
+    const SubMaps &mp = maps[p];
+    const int64_t ro = d.row_off;
+    int t_own = 0;
+    // local CSR of A_p (for ILU) built alongside the ELL arrays
+    std::vector<int32_t> lrp, lci;
+    std::vector<double> lva;
+    if (kind == RAS_LOCAL_ILU0_CG) lrp.push_back(0);
+    for (int i = 0; i < d.n; ++i) {
+      const int g = mp.omega[i];
+      gidx[ro + i] = g;
+      ownf[ro + i] = mp.owned[i];
+      if (mp.owned[i]) own[d.own_off + t_own++] = i;
+      int k = 0, kl = 0;
+      for (int e = A->row_ptr[g]; e < A->row_ptr[g + 1]; ++e, ++k) {
+        const int col = A->col_idx[e];
+        rcol[ro * K + (int64_t)k * d.npad + i] = col;
+        rval[ro * K + (int64_t)k * d.npad + i] = A->val[e];
+        const int j = local_index(mp.omega, col);
+        if (j < 0) continue;
+        if (kind == RAS_LOCAL_BANDCHOL) {
+          if (j <= i) band[band_off[p] + (int64_t)i * (mp.w + 1) + (j - i + mp.w)] = A->val[e];
+        } else {
+          lcol[ro * K + (int64_t)kl * d.npad + i] = j;
+          lval64[ro * K + (int64_t)kl * d.npad + i] = A->val[e];
+          if (kind == RAS_LOCAL_ILU0_CG) {
+            lci.push_back(j);
+            lva.push_back(A->val[e]);
+          }
+          ++kl;
+        }
+      }
+      for (; k < K; ++k) rcol[ro * K + (int64_t)k * d.npad + i] = g;  // zero-valued padding
+      if (kind != RAS_LOCAL_BANDCHOL)
+        for (; kl < K; ++kl) lcol[ro * K + (int64_t)kl * d.npad + i] = i;
+      if (kind == RAS_LOCAL_ILU0_CG) lrp.push_back((int32_t)lci.size());
+    }
+    for (int i = d.n; i < d.npad; ++i) {
+      gidx[ro + i] = mp.omega[0];
+      for (int k = 0; k < K; ++k) {
+        rcol[ro * K + (int64_t)k * d.npad + i] = mp.omega[0];
+        if (kind != RAS_LOCAL_BANDCHOL) lcol[ro * K + (int64_t)k * d.npad + i] = i < d.n ? i : 0;
+      }
+    }
+    for (size_t q = 0; q < mp.nbr.size(); ++q) nbr[d.nbr_off + q] = mp.nbr[q];
+    if (kind == RAS_LOCAL_ILU0_CG) {
+      std::vector<double> f = lva;
+      if (!ilu0_local(d.n, lrp, lci, f)) {
+        ilu_fail = 1;
+        return;
+      }
+      // scatter the factors into the ELL layout (same column order as lcol)
+      for (int i = 0; i < d.n; ++i)
+        for (int e = lrp[i], kl = 0; e < lrp[i + 1]; ++e, ++kl)
+          lu64[ro * K + (int64_t)kl * d.npad + i] = f[e];
+      std::vector<int32_t> pf, rf, pb, rb;
+      level_schedule(d.n, lrp, lci, pf, rf, pb, rb);
+      lev_ptr[p] = pf;
+      lev_ptr[p].insert(lev_ptr[p].end(), pb.begin(), pb.end());
+      lev_rows[p] = rf;
+      lev_rows[p].insert(lev_rows[p].end(), rb.begin(), rb.end());
+    }
+  });
+  if (ilu_fail) return RAS_ENOTSPD;
+  std::vector<int32_t> levp_all, levr_all;
+  if (kind == RAS_LOCAL_ILU0_CG) {
+    for (int p = 0; p < P; ++p) {
+      SubDesc &d = c->subs[p];
+      d.lev_off = levp;
+      d.lrow_off = levr;
+      // forward pointer array has nlev_f + 1 entries, backward nlev_b + 1
+      const std::vector<int32_t> &lp = lev_ptr[p];
+      // split point: the forward array ends where its last entry equals n
+      int nf = 0;
+      while (lp[nf] != d.n) ++nf;
+      d.nlev_f = nf;
+      d.nlev_b = (int)lp.size() - (nf + 1) - 1;
+      levp += (int64_t)lp.size();
+      levr += (int64_t)lev_rows[p].size();
+      levp_all.insert(levp_all.end(), lp.begin(), lp.end());
+      levr_all.insert(levr_all.end(), lev_rows[p].begin(), lev_rows[p].end());
+    }
+  }
+  std::vector<int> band_w(P);
+  for (int p = 0; p < P; ++p) band_w[p] = maps[p].w;
+  for (int p = 0; p < P; ++p) {
+    c->omega.push_back(std::move(maps[p].omega));
+    c->owned.push_back(std::move(maps[p].owned));
+    c->iface.push_back(std::move(maps[p].iface));
+  }
+
+  // ---- device upload
+  CUDA_TRY(cudaEventCreate(&c->ev0));
+  CUDA_TRY(cudaEventCreate(&c->ev1));
+  if ((st = c->upload(c->d_subs, c->subs)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_sub, P)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_st, 1)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_gidx, gidx)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_ownf, ownf)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_rcol, rcol)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_rval, rval)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_own, own)) != RAS_OK) return st;
+  if ((st = c->upload(c->d_nbr, nbr)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_xalt, n)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_ctl, 1)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_sysdesc, 1)) != RAS_OK) return st;
+  CUDA_TRY(cudaMallocHost(&c->h_sysdesc, sizeof(SysDesc)));
+  CUDA_TRY(cudaMallocHost(&c->h_ctl, sizeof(GridCtl)));
+  CUDA_TRY(cudaMallocHost(&c->h_st, sizeof(SysState)));
+  CUDA_TRY(cudaMallocHost(&c->h_sub, sizeof(SubState) * P));
+  CUDA_TRY(cudaMemsetAsync(c->d_ctl, 0, sizeof(GridCtl), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->d_xalt, 0, sizeof(double) * n, c->stream));
+
+  if (kind == RAS_LOCAL_BANDCHOL) {
+    // factorise on the GPU in FP64, then lay out the slabs in the storage precision
+    double *d_band = nullptr;
+    BandJob *d_jobs = nullptr;
+    LayoutJob *d_ljobs = nullptr;
+    std::vector<BandJob> jobs(P);
+    std::vector<LayoutJob> ljobs;
+    int maxw = 0;
+    for (int p = 0; p < P; ++p) {
+      const SubDesc &d = c->subs[p];
+      const int w = band_w[p];
+      jobs[p] = {d.n, w, band_off[p]};
+      maxw = std::max(maxw, w);
+      for (int Kb = 0; Kb < d.npad / 32; ++Kb) {
+        LayoutJob lj{};
+        lj.n = d.n;
+        lj.w = w;
+        lj.W = d.W;
+        lj.K = Kb;
+        lj.nb = d.npad / 32;
+        lj.band_off = band_off[p];
+        lj.fac_off = d.fac_off;
+        ljobs.push_back(lj);
+      }
+    }
+    CUDA_TRY(cudaMalloc(&d_band, std::max<size_t>(band.size(), 1) * sizeof(double)));
+    CUDA_TRY(cudaMalloc(&d_jobs, jobs.size() * sizeof(BandJob)));
+    CUDA_TRY(cudaMalloc(&d_ljobs, ljobs.size() * sizeof(LayoutJob)));
+    CUDA_TRY(cudaMemcpyAsync(d_band, band.data(), band.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(BandJob),
+                             cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(d_ljobs, ljobs.data(), ljobs.size() * sizeof(LayoutJob),
+                             cudaMemcpyHostToDevice, c->stream));
+    void *d_fac = nullptr;
+    const size_t fbytes = std::max<int64_t>(fac, 1) * prec_bytes(prec);
+    cudaError_t e = cudaMalloc(&d_fac, fbytes);
+    if (e != cudaSuccess) {
+      cudaFree(d_band); cudaFree(d_jobs); cudaFree(d_ljobs);
+      return RAS_ENOMEM;
+    }
+    c->bufs.push_back({d_fac, fbytes});
+    c->device_bytes += (int64_t)fbytes;
+    c->d_fac = d_fac;
+    e = launch_band_chol(d_jobs, P, maxw, d_band, c->d_ctl, c->stream);
+    if (e == cudaSuccess) e = launch_band_layout(prec, d_ljobs, (int)ljobs.size(), d_band, d_fac, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_band);
+    cudaFree(d_jobs);
+    cudaFree(d_ljobs);
+    if (e != cudaSuccess) {
+      last_cuda_error() = e;
+      return RAS_ECUDA;
+    }
+    if (c->h_ctl->status != 0) return (ras_status)c->h_ctl->status;
+  } else {
+    std::vector<int32_t> &lc = lcol;
+    if ((st = c->upload(c->d_lcol, lc)) != RAS_OK) return st;
+    auto up_prec = [&](void *&dst, const std::vector<double> &src) -> ras_status {
+      const size_t bytes = std::max<size_t>(src.size(), 1) * prec_bytes(prec);
+      std::vector<unsigned char> tmp(bytes);
+      for (size_t k = 0; k < src.size(); ++k) store_prec(tmp.data(), k, prec, src[k]);
+      unsigned char *d = nullptr;
+      ras_status s2 = c->upload(d, tmp);
+      dst = d;
+      return s2;
+    };
+    if ((st = up_prec(c->d_lval, lval64)) != RAS_OK) return st;
+    if (kind == RAS_LOCAL_ILU0_CG) {
+      if ((st = up_prec(c->d_lu, lu64)) != RAS_OK) return st;
+      if ((st = c->upload(c->d_levp, levp_all)) != RAS_OK) return st;
+      if ((st = c->upload(c->d_levr, levr_all)) != RAS_OK) return st;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+
+  // ---- default launch plan: one system, all subdomains
+  std::vector<Item> items(P);
+  for (int p = 0; p < P; ++p) items[p] = {0, p, 0, 0};
+  st = plan_launch(c->plan, kind, prec, items, c->cost, c->plan.Wmax, npad_max, c->stream);
+  if (st != RAS_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->last_updates.assign(P, 0);
+  *out = c.release();
+  return RAS_OK;
+}
+
+namespace {
+
+// Runs one full solve of the systems described by `sysdesc` with plan `pl`.
+ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &pl,
+                     SysDesc *d_sys, int nsys, GridCtl *d_ctl, GridCtl *h_ctl, int32_t mode,
+                     int64_t max_updates, int m, cudaEvent_t ev0, cudaEvent_t ev1) {
+  Launch L{};
+  L.sys = d_sys;
+  L.nsys = nsys;
+  L.mode = mode;
+  L.items = pl.d_items;
+  L.cta_off = pl.d_cta_off;
+  L.cta_sys = pl.d_cta_sys;
+  L.cta_sys_off = pl.d_cta_sys_off;
+  L.ctl = d_ctl;
+  L.max_updates = max_updates > 0 ? max_updates : 1000000;
+  L.step_limit = (int64_t)1 << 62;
+  L.timeout_ns = timeout_ns();
+  L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
+  L.max_restarts = 8;
+  L.m = m;
+  L.Wmax = pl.Wmax;
+  L.npad_max = pl.npad_max;
+  L.persist = 1;
+  std::memset(h_ctl, 0, sizeof(GridCtl));
+  h_ctl->remaining = nsys;
+  const int nitems = (int)pl.items.size();
+  CUDA_TRY(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaEventRecord(ev0, stream));
+  CUDA_TRY(launch_init(L, nitems, stream));
+  CUDA_TRY(launch_main(kind, prec, pl.nt, L, pl.grid, pl.smem, stream));
+  if (mode == RAS_SYNC) CUDA_TRY(launch_copyback(L, nitems, stream));
+  CUDA_TRY(cudaEventRecord(ev1, stream));
+  CUDA_TRY(launch_residual(L, nitems, stream));
+  return RAS_OK;
+}
+
+ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const SubState *sub,
+                       int32_t mode, ras_solve_info *info, float ms) {
+  ras_status rs = RAS_OK;
+  if (ctl.status != 0) rs = (ras_status)ctl.status;
+  else if (st.status != 0) rs = (ras_status)st.status;
+  std::vector<int64_t> u(c->P);
+  for (int p = 0; p < c->P; ++p) u[p] = sub[p].updates;
+  c->last_updates = u;
+  if (info) {
+    std::vector<int64_t> s(u);
+    std::sort(s.begin(), s.end());
+    info->updates_min = s.front();
+    info->updates_max = s.back();
+    info->updates_median = s[s.size() / 2];
+    info->iterations = mode == RAS_SYNC ? st.iters : info->updates_median;
+    info->relres = st.b2 > 0 ? std::sqrt(st.res2 / st.b2) : std::sqrt(st.res2);
+    info->solve_ms = ms;
+    info->restarts = st.restarts;
+    info->status = rs;
+  }
+  return rs;
+}
+
+}  // namespace
+
+ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t mode,
+                     int64_t max_updates, ras_solve_info *info) {
+  if (!c || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC)) return RAS_EINVAL;
+  if (info) std::memset(info, 0, sizeof(*info));
+  *c->h_sysdesc = make_sysdesc(c, b, x, tol);
+  CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
+                           c->stream));
+  ras_status rs = run_solve(c->stream, c->ls.kind, c->ls.prec, c->plan, c->d_sysdesc, 1, c->d_ctl,
+                            c->h_ctl, mode, max_updates, c->ls.inner_iters, c->ev0, c->ev1);
+  if (rs != RAS_OK) return rs;
+  CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->h_sub, c->d_sub, sizeof(SubState) * c->P, cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  return finish_info(c, *c->h_st, *c->h_ctl, c->h_sub, mode, info, ms);
+}
+
+ras_status ras_solve_host(ras_ctx *c, const double *b_host, double *x_host, double tol,
+                          int32_t mode, int64_t max_updates, ras_solve_info *info) {
+  if (!c || !b_host || !x_host) return RAS_EINVAL;
+  if (!c->d_bx) {
+    ras_status s = c->alloc(c->d_bx, 2 * (size_t)c->n);
+    if (s != RAS_OK) return s;
+  }
+  double *db = c->d_bx, *dx = c->d_bx + c->n;
+  CUDA_TRY(cudaMemcpyAsync(db, b_host, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(dx, x_host, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+  ras_status rs = ras_solve(c, db, dx, tol, mode, max_updates, info);
+  if (rs != RAS_OK && rs != RAS_ENOCONV) return rs;
+  CUDA_TRY(cudaMemcpyAsync(x_host, dx, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return rs;
+}
+
+ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *const *b,
+                           double *const *x, double tol, int32_t mode, int64_t max_updates,
+                           ras_solve_info *infos) {
+  if (!ctxs || num <= 0 || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC))
+    return RAS_EINVAL;
+  for (int s = 0; s < num; ++s)
+    if (!ctxs[s] || !b[s] || !x[s] || ctxs[s]->ls.kind != ctxs[0]->ls.kind ||
+        ctxs[s]->ls.prec != ctxs[0]->ls.prec || ctxs[s]->ls.inner_iters != ctxs[0]->ls.inner_iters)
+      return RAS_EINVAL;
+  ras_ctx *c0 = ctxs[0];
+  cudaStream_t stream = c0->stream;
+  std::vector<Item> items;
+  std::vector<double> cost;
+  std::vector<SysDesc> sd(num);
+  int Wmax = 0, npad_max = 0;
+  for (int s = 0; s < num; ++s) {
+    ras_ctx *c = ctxs[s];
+    // one solve at a time per context: the state buffers are per context
+    for (int t = 0; t < s; ++t)
+      if (ctxs[t] == c) return RAS_EINVAL;
+    sd[s] = make_sysdesc(c, b[s], x[s], tol);
+    for (int p = 0; p < c->P; ++p) {
+      items.push_back({s, p, 0, 0});
+      cost.push_back(c->cost[p]);
+    }
+    Wmax = std::max(Wmax, c->plan.Wmax);
+    npad_max = std::max(npad_max, c->plan.npad_max);
+  }
+  LaunchPlan pl;
+  ras_status rs = plan_launch(pl, c0->ls.kind, c0->ls.prec, items, cost, Wmax, npad_max, stream);
+  if (rs != RAS_OK) {
+    pl.release();
+    return rs;
+  }
+  SysDesc *d_sys = nullptr;
+  GridCtl *d_ctl = nullptr;
+  GridCtl h_ctl{};
+  std::vector<SysState> hst(num);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(stream);
+    cudaFree(d_sys);
+    cudaFree(d_ctl);
+    pl.release();
+  };
+  if (cudaMalloc(&d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+      cudaMalloc(&d_ctl, sizeof(GridCtl)) != cudaSuccess) {
+    cleanup();
+    return RAS_ENOMEM;
+  }
+  cudaMemcpyAsync(d_sys, sd.data(), sizeof(SysDesc) * num, cudaMemcpyHostToDevice, stream);
+  rs = run_solve(stream, c0->ls.kind, c0->ls.prec, pl, d_sys, num, d_ctl, &h_ctl, mode,
+                 max_updates, c0->ls.inner_iters, c0->ev0, c0->ev1);
+  if (rs != RAS_OK) {
+    cleanup();
+    return rs;
+  }
+  cudaMemcpyAsync(&h_ctl, d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, stream);
+  std::vector<std::vector<SubState>> hsub(num);
+  for (int s = 0; s < num; ++s) {
+    hsub[s].resize(ctxs[s]->P);
+    cudaMemcpyAsync(&hst[s], ctxs[s]->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(hsub[s].data(), ctxs[s]->d_sub, sizeof(SubState) * ctxs[s]->P,
+                    cudaMemcpyDeviceToHost, stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(stream);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c0->ev0, c0->ev1);
+  cleanup();
+  if (e != cudaSuccess) return RAS_ECUDA;
+  ras_status first = RAS_OK;
+  for (int s = 0; s < num; ++s) {
+    ras_status r = finish_info(ctxs[s], hst[s], h_ctl, hsub[s].data(), mode,
+                               infos ? &infos[s] : nullptr, ms);
+    if (first == RAS_OK && r != RAS_OK) first = r;
+  }
+  return first;
+}
+
+ras_status ras_get_maps(const ras_ctx *c, int32_t p, const int32_t **omega, int32_t *n_omega,
+                        const uint8_t **owned_mask, const int32_t **iface, int32_t *n_iface) {
+  if (!c || p < 0 || p >= c->P || !omega || !n_omega || !owned_mask || !iface || !n_iface)
+    return RAS_EINVAL;
+  *omega = c->omega[p].data();
+  *n_omega = (int32_t)c->omega[p].size();
+  *owned_mask = c->owned[p].data();
+  *iface = c->iface[p].data();
+  *n_iface = (int32_t)c->iface[p].size();
+  return RAS_OK;
+}
+
+ras_status ras_get_info(const ras_ctx *c, int32_t *num_parts, int32_t *n, int32_t *max_bandwidth,
+                        int64_t *device_bytes) {
+  if (!c) return RAS_EINVAL;
+  if (num_parts) *num_parts = c->P;
+  if (n) *n = c->n;
+  if (max_bandwidth) *max_bandwidth = c->maxw;
+  if (device_bytes) *device_bytes = c->device_bytes;
+  return RAS_OK;
+}
+
+ras_status ras_get_update_counts(const ras_ctx *c, int64_t *counts) {
+  if (!c || !counts) return RAS_EINVAL;
+  std::copy(c->last_updates.begin(), c->last_updates.end(), counts);
+  return RAS_OK;
+}
+
+ras_status ras_relres(ras_ctx *c, const double *b, const double *x, double *relres) {
+  if (!c || !b || !x || !relres) return RAS_EINVAL;
+  *c->h_sysdesc = make_sysdesc(c, b, const_cast<double *>(x), 1.0);
+  CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
+                           c->stream));
+  Launch L{};
+  L.sys = c->d_sysdesc;
+  L.nsys = 1;
+  L.items = c->plan.d_items;
+  const int nitems = (int)c->plan.items.size();
+  CUDA_TRY(launch_init(L, nitems, c->stream));
+  CUDA_TRY(launch_residual(L, nitems, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const SysState &st = *c->h_st;
+  *relres = st.b2 > 0 ? std::sqrt(st.res2 / st.b2) : std::sqrt(st.res2);
+  return RAS_OK;
+}
+
+}  // extern "C"

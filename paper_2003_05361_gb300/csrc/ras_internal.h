@@ -1,0 +1,140 @@
+// Internal data layout shared by the host setup code and the device kernels.
+//
+// Device-side layout of one context (one linear system, P subdomains):
+//   * per-subdomain descriptors SubDesc[P] and runtime state SubState[P];
+//   * per-local-row arrays concatenated over subdomains, each subdomain padded
+//     to a multiple of 32 rows (npad): gidx (global id of local row i),
+//     ownf (1 when the row is owned, i.e. in O_p);
+//   * the residual operator of Omega_p's rows in ELL form with GLOBAL columns
+//     (rcol/rval, K entries per row, column-major inside a subdomain:
+//     entry k of local row i at row_off*K + k*npad + i). It computes
+//     r_p = b[Omega_p] - A[Omega_p, :] x, reading x on Omega_p and E_p;
+//   * the owned-row list own_l (local ids);
+//   * local-solver data: banded-Cholesky slabs (fac), or the local matrix A_p
+//     in ELL form with LOCAL columns (lcol/lval) plus ILU(0) factors (luval)
+//     and level schedules.
+#pragma once
+#include <stdint.h>
+
+namespace ras {
+
+enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2 };
+enum Prec : int32_t { kF64 = 0, kF32 = 1, kBF16 = 2 };
+enum Mode : int32_t { kSync = 0, kAsync = 1 };
+// status codes (mirror ras_status)
+enum : int32_t { kOK = 0, kEINVAL = 1, kENOMEM = 2, kENOTSPD = 3, kENOCONV = 4, kETIMEOUT = 5,
+                 kECUDA = 6, kENOTSUP = 7 };
+// async per-system phases
+enum : int32_t { kRun = 0, kDrain = 1, kCheck = 2, kDone = 3 };
+
+struct SubDesc {
+  int32_t n;        // |Omega_p|
+  int32_t npad;     // n rounded up to a multiple of 32
+  int32_t n_own;    // |O_p|
+  int32_t W;        // band: storage half-width (>= 31); slab = (W+1)*32 entries
+  int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
+  int64_t own_off;  // offset into own_l
+  int64_t fac_off;  // band: first slab (entries); forward slabs then backward
+  int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
+  int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
+  int32_t nlev_f;   // ILU: number of forward / backward levels
+  int32_t nlev_b;
+  int32_t nbr_off;  // neighbour subdomains (system-local ids) in nbr[]
+  int32_t n_nbr;
+};
+
+struct SubState {
+  double bloc2;       // ||b||^2 over Omega_p (local criterion, Eq. 2)
+  double bown2;       // ||b||^2 over O_p
+  double part[2];     // owned-row residual^2 partials
+  int64_t updates;    // local solves in the current solve
+  int64_t step_updates;  // local solves in the current launch
+  int64_t stale;      // async: solves that saw no new neighbour data
+  uint64_t nbr_seen;  // async: sum of neighbour versions at the last solve
+  uint32_t version;   // async: published update counter (release store)
+  int32_t conv_epoch; // async: epoch in which Eq. 2 last held (-1: not converged)
+  int32_t park_epoch;
+  int32_t check_epoch;
+};
+
+struct SysState {
+  double b2;          // ||b||^2
+  double res2;        // last global residual^2
+  int64_t iters;      // sync: completed RAS iterations
+  uint32_t word;      // async: (epoch << 2) | phase
+  int32_t status;
+  int32_t done;       // sync: finished (converged or failed)
+  int32_t nconv;      // async counters
+  int32_t nparked;
+  int32_t nchecked;
+  int32_t restarts;
+  int32_t result_alt; // sync: result left in xalt (copied back by the epilogue)
+};
+
+struct SysDesc {
+  const double *b;
+  double *x;     // initial guess in, result out
+  double *xalt;  // sync double buffer
+  int32_t n;
+  int32_t P;
+  int32_t K;     // ELL width
+  int32_t pad_;
+  double tol2;
+  const SubDesc *subs;
+  SubState *sub;
+  SysState *st;
+  const int32_t *gidx;
+  const uint8_t *ownf;
+  const int32_t *rcol;
+  const double *rval;
+  const int32_t *own_l;
+  const void *fac;
+  const int32_t *lcol;
+  const void *lval;
+  const void *luval;
+  const int32_t *lev_ptr;
+  const int32_t *lev_rows;
+  const int32_t *nbr;
+};
+
+struct Item {
+  int32_t sys;  // system index in the launch
+  int32_t p;    // subdomain id within the system
+  int32_t ls;   // index of `sys` in the owning CTA's system list
+  int32_t pad_;
+};
+
+constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
+
+struct GridCtl {
+  unsigned int count;  // barrier arrivals
+  unsigned int gen;    // barrier generation
+  int fin_accum;       // systems finished since the last barrier
+  int remaining;       // systems still running (published by the barrier)
+  int abort;           // set on any device-side error
+  int status;          // first error code
+  unsigned long long err_info;
+};
+
+struct Launch {
+  SysDesc *sys;
+  int32_t nsys;
+  int32_t mode;
+  const Item *items;
+  const int32_t *cta_off;      // [G+1]
+  const int32_t *cta_sys;      // distinct systems per CTA (sync decisions)
+  const int32_t *cta_sys_off;  // [G+1]
+  GridCtl *ctl;
+  int64_t max_updates;         // per subdomain (async) / iterations (sync)
+  int64_t step_limit;          // local updates (async) or iterations (sync) in this launch
+  int64_t timeout_ns;          // limit on any device-side wait
+  int64_t solve_limit_ns;      // limit on the whole launch (then RAS_ETIMEOUT)
+  int32_t max_restarts;
+  int32_t m;                   // CG / PCG steps
+  int32_t Wmax;                // band: max W over the launch
+  int32_t npad_max;
+  int32_t persist;             // async: keep polling until every system is done
+  int32_t pad_;
+};
+
+}  // namespace ras

@@ -1,0 +1,1206 @@
+// Device code of the GB300 Restricted Additive Schwarz solver (sm_103a).
+//
+// Kernels:
+//   band_chol_kernel     setup: banded Cholesky A_p = L L^T in FP64, one CTA per
+//                        subdomain, sliding (w+1)x(w+1) window in shared memory
+//                        (direct local solver of Sec. 3.3.1, factorised once).
+//   band_layout_kernel   setup: turns L into the slab layout read by the
+//                        triangular solves (inverted 32x32 diagonal blocks),
+//                        rounded to the storage precision (FP64 / FP32 / BF16).
+//   ras_init_kernel      per solve: ||b||^2 over Omega_p and O_p, state reset.
+//   ras_sysnorm_kernel   per solve: per-system sums in a fixed order.
+//   ras_main_kernel      the persistent RAS kernel, one CTA per group of
+//                        subdomains. RAS_SYNC: iterations separated by a
+//                        grid-wide barrier (synchronous Schwarz, Sec. 2.1).
+//                        RAS_ASYNC: no barrier; owned values are published with
+//                        a release store of a per-subdomain version counter and
+//                        neighbours acquire it before reading (asynchronous
+//                        Schwarz, Sec. 2.1 / one-sided exchange of Sec. 3.4);
+//                        convergence by the local criterion of Eq. 2, a global
+//                        converged counter, and the post-termination global
+//                        check of Sec. 3.3.2.
+//   ras_residual_kernel  ||b - A x||^2 partials over owned rows.
+//   ras_copyback_kernel  moves a sync result left in the second buffer to x.
+//
+// Every device-side wait (grid barrier, mbarrier, idle polling) is bounded by
+// a %globaltimer limit; on expiry the kernel records RAS_ETIMEOUT in GridCtl,
+// raises the abort flag, drains its own bulk copies and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ras_internal.h"
+#include "ras_launch.h"
+
+namespace ras {
+
+// --------------------------------------------------------------------------
+// small PTX helpers
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed_f64(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double *p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void set_error(GridCtl *c, int code, unsigned long long info) {
+  if (atomicCAS(&c->status, 0, code) == 0) c->err_info = info;
+  atomicExch(&c->abort, 1);
+}
+
+template <typename T> struct CTypeOf { using type = float; };
+template <> struct CTypeOf<double> { using type = double; };
+
+template <typename T> __device__ __forceinline__ T from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+__device__ __forceinline__ float to_ct(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_ct(float v) { return v; }
+__device__ __forceinline__ double to_ct(double v) { return v; }
+
+// Deterministic CTA reduction: butterfly inside each warp, then every thread
+// adds the per-warp values in the same order, so all threads hold the same
+// bit pattern. red must hold NT/32 values.
+template <int NT, typename V>
+__device__ __forceinline__ V block_sum(V v, V *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  V s = red[0];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = a;
+    red[NT / 32 + (threadIdx.x >> 5)] = b;
+  }
+  __syncthreads();
+  double sa = red[0], sb = red[NT / 32];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) {
+    sa += red[i];
+    sb += red[NT / 32 + i];
+  }
+  a = sa;
+  b = sb;
+}
+
+// Fixed-order sum of the P per-subdomain partials of one system by one warp
+// (lane-strided sequential sums, then a butterfly). Same bits in every CTA.
+__device__ __forceinline__ double warp_sum_partials(const SubState *sub, int P, int slot,
+                                                    bool relaxed) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int p = lane; p < P; p += 32)
+    s += relaxed ? ld_relaxed_f64(&sub[p].part[slot]) : sub[p].part[slot];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// --------------------------------------------------------------------------
+// grid barrier (co-resident CTAs of a cooperative launch)
+// --------------------------------------------------------------------------
+
+// All CTAs arrive; `fin` systems finished by this CTA since the last barrier
+// are folded into GridCtl::remaining by the last arriver before it releases
+// the generation, so every CTA reads the same `remaining` afterwards.
+__device__ bool grid_barrier(GridCtl *c, int fin, int64_t timeout_ns, int *s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (fin) atomicAdd(&c->fin_accum, fin);
+    const uint32_t gen = ld_acquire_u32(&c->gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&c->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      c->count = 0;
+      const int f = atomicExch(&c->fin_accum, 0);
+      if (f) atomicSub(&c->remaining, f);
+      __threadfence();
+      st_release_u32(&c->gen, gen + 1);
+    } else {
+      const uint64_t t0 = gtimer();
+      uint32_t spins = 0;
+      while (ld_acquire_u32(&c->gen) == gen) {
+        if ((++spins & 63u) == 0) {
+          if (ld_relaxed_s32(&c->abort)) { ok = 0; break; }
+          if ((int64_t)(gtimer() - t0) > timeout_ns) {
+            set_error(c, kETIMEOUT, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    if (ld_relaxed_s32(&c->abort)) ok = 0;
+    s_flag[0] = ok;
+    s_flag[1] = ld_relaxed_s32(&c->remaining);
+  }
+  __syncthreads();
+  return s_flag[0] != 0;
+}
+
+// --------------------------------------------------------------------------
+// bulk-copy (TMA) helpers for the band slabs
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; returns false on timeout (error recorded by the caller).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_t timeout_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if ((int64_t)(gtimer() - t0) > timeout_ns) return false;
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// setup: banded Cholesky (FP64)
+// --------------------------------------------------------------------------
+
+// band (row-major, ld = w+1): band[i*ld + t] = A[i][i-w+t]; overwritten by L.
+// Right-looking: for column j, L_jj = sqrt(a_jj), L_ij = a_ij / L_jj for
+// i in (j, j+w], then a_ik -= L_ij L_kj on the trailing triangle. Rows j..j+w
+// live in a circular window of shared memory (slot = row mod (w+1)).
+__global__ void __launch_bounds__(256) band_chol_kernel(const BandJob *jobs, double *band,
+                                                        GridCtl *ctl) {
+  extern __shared__ __align__(16) double win[];
+  __shared__ double s_piv;
+  __shared__ int s_bad;
+  const BandJob jb = jobs[blockIdx.x];
+  const int n = jb.n, w = jb.w, ld = w + 1;
+  double *B = band + jb.band_off;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int e = tid; e < ld * ld; e += NT) {
+    const int r = e / ld;
+    win[e] = r < n ? B[(int64_t)r * ld + (e % ld)] : 0.0;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int sj = j % ld;
+    if (j > 0) {
+      // row j-1 is final: write it out, load row j+w into its slot
+      const int sp = (j - 1) % ld;
+      const int rin = j + w;
+      for (int t = tid; t < ld; t += NT) {
+        B[(int64_t)(j - 1) * ld + t] = win[sp * ld + t];
+        win[sp * ld + t] = rin < n ? B[(int64_t)rin * ld + t] : 0.0;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const double a = win[sj * ld + w];
+      if (!(a > 0.0)) {
+        s_bad = 1;
+      } else {
+        const double d = sqrt(a);
+        win[sj * ld + w] = d;
+        s_piv = d;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double d = s_piv;
+    const int nr = min(w, n - 1 - j);  // rows j+1 .. j+nr
+    for (int q = tid; q < nr; q += NT) {
+      const int i = j + 1 + q;
+      win[(i % ld) * ld + (j - i + w)] /= d;
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * nr; e += NT) {
+      const int qi = e / nr, qk = e % nr;
+      if (qk > qi) continue;
+      const int i = j + 1 + qi, k = j + 1 + qk;
+      const int si = i % ld, sk = k % ld;
+      win[si * ld + (k - i + w)] -= win[si * ld + (j - i + w)] * win[sk * ld + (j - k + w)];
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) set_error(ctl, kENOTSPD, (unsigned long long)blockIdx.x);
+    return;
+  }
+  // flush the last row
+  if (n > 0) {
+    const int sl = (n - 1) % ld;
+    for (int t = tid; t < ld; t += NT) B[(int64_t)(n - 1) * ld + t] = win[sl * ld + t];
+  }
+}
+
+// --------------------------------------------------------------------------
+// setup: slab layout for the blocked triangular solves
+// --------------------------------------------------------------------------
+//
+// Rows are grouped in blocks of 32. With W = storage half-width (>= 31 and
+// >= the true half-width w), block K's FORWARD slab F[t][l] (t = 0..W,
+// l = 0..31, row i = 32K + l) holds
+//   t <  W - l : L[i][i - W + t]            (columns left of the block)
+//   t >= W - l : Linv_KK[l][l - (W - t)]    (inverse of the diagonal block)
+// and its BACKWARD slab Bk[d][l] holds, for U = L^T,
+//   d <  32 - l : Uinv_KK[l][l + d] = Linv_KK[l + d][l]
+//   d >= 32 - l : U[i][i + d] = L[i + d][i] (columns right of the block)
+// so the forward step of block K is  y_K = Linv_KK (r_K - L_{K,left} y_left)
+// and the backward step  z_K = Uinv_KK (y_K - U_{K,right} z_right), each row
+// reading exactly w+1 useful entries. Rows i >= n are identity rows.
+template <typename T>
+__global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
+                                                         const double *band, T *fac) {
+  __shared__ double Lkk[32][33];
+  __shared__ double X[32][33];
+  const LayoutJob jb = jobs[blockIdx.x];
+  const int l = threadIdx.x;
+  const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, ld = w + 1;
+  const double *Bd = band + jb.band_off;
+  const int i = 32 * K + l;
+  // diagonal block, row l
+  for (int m = 0; m < 32; ++m) {
+    double v = 0.0;
+    const int jcol = 32 * K + m;
+    if (i < n) {
+      if (m <= l && l - m <= w) v = Bd[(int64_t)i * ld + (jcol - i + w)];
+    } else if (m == l) {
+      v = 1.0;
+    }
+    Lkk[l][m] = v;
+  }
+  __syncwarp();
+  // lane m computes column m of the inverse by forward substitution
+  {
+    const int m = l;
+    double col[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      double s = (r == m) ? 1.0 : 0.0;
+      if (r >= m) {
+        for (int k = m; k < r; ++k) s -= Lkk[r][k] * col[k];
+        col[r] = s / Lkk[r][r];
+      } else {
+        col[r] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) X[r][m] = col[r];
+  }
+  __syncwarp();
+  const int64_t slab = (int64_t)(W + 1) * 32;
+  T *F = fac + jb.fac_off + (int64_t)K * slab;
+  T *Bk = fac + jb.fac_off + (int64_t)jb.nb * slab + (int64_t)K * slab;
+  for (int t = 0; t <= W; ++t) {
+    double v;
+    if (t < W - l) {
+      const int jcol = i - W + t;
+      const int tb = t - W + w;  // index in the stored band row
+      v = (i < n && jcol >= 0 && tb >= 0) ? Bd[(int64_t)i * ld + tb] : 0.0;
+    } else {
+      v = X[l][l - (W - t)];
+    }
+    F[(int64_t)t * 32 + l] = from_double<T>(v);
+  }
+  for (int d = 0; d <= W; ++d) {
+    double v;
+    if (d < 32 - l) {
+      v = X[l + d][l];
+    } else {
+      const int r = i + d;
+      v = (i < n && r < n && d <= w) ? Bd[(int64_t)r * ld + (w - d)] : 0.0;
+    }
+    Bk[(int64_t)d * 32 + l] = from_double<T>(v);
+  }
+}
+
+// --------------------------------------------------------------------------
+// per-solve helpers
+// --------------------------------------------------------------------------
+
+// One CTA per item: ||b||^2 over Omega_p and O_p, reset of the subdomain state.
+__global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
+  __shared__ double red[8];
+  const Item it = L.items[blockIdx.x];
+  const SysDesc S = L.sys[it.sys];
+  const SubDesc D = S.subs[it.p];
+  double a = 0.0, o = 0.0;
+  for (int i = threadIdx.x; i < D.n; i += 128) {
+    const double v = S.b[S.gidx[D.row_off + i]];
+    a += v * v;
+    if (S.ownf[D.row_off + i]) o += v * v;
+  }
+  block_sum2<128>(a, o, red);
+  if (threadIdx.x == 0) {
+    SubState &s = S.sub[it.p];
+    s.bloc2 = a;
+    s.bown2 = o;
+    s.part[0] = s.part[1] = 0.0;
+    s.updates = 0;
+    s.step_updates = 0;
+    s.stale = 0;
+    s.nbr_seen = 0;
+    s.version = 0;
+    s.conv_epoch = -1;
+    s.park_epoch = -1;
+    s.check_epoch = -1;
+  }
+}
+
+// One warp per system: b2 = sum of the owned partials in subdomain order,
+// state reset (what = 0), or res2 from part[0] (what = 1).
+__global__ void ras_sysnorm_kernel(Launch L, int what) {
+  const int s = blockIdx.x;
+  if (s >= L.nsys) return;
+  const SysDesc S = L.sys[s];
+  const int lane = threadIdx.x;
+  double acc = 0.0;
+  for (int p = lane; p < S.P; p += 32) acc += what == 0 ? S.sub[p].bown2 : S.sub[p].part[0];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    if (what == 0) {
+      S.st->b2 = acc;
+      S.st->res2 = 0.0;
+      S.st->iters = 0;
+      S.st->word = kRun;
+      S.st->status = 0;
+      S.st->done = 0;
+      S.st->nconv = 0;
+      S.st->nparked = 0;
+      S.st->nchecked = 0;
+      S.st->restarts = 0;
+      S.st->result_alt = 0;
+    } else {
+      S.st->res2 = acc;
+    }
+  }
+}
+
+// One CTA per item: owned-row residual partial of the system's x.
+__global__ void __launch_bounds__(128) ras_residual_kernel(Launch L) {
+  __shared__ double red[8];
+  const Item it = L.items[blockIdx.x];
+  const SysDesc S = L.sys[it.sys];
+  const SubDesc D = S.subs[it.p];
+  const int K = S.K;
+  const int64_t eb = D.row_off * K;
+  double o = 0.0, dummy = 0.0;
+  for (int i = threadIdx.x; i < D.n; i += 128) {
+    if (!S.ownf[D.row_off + i]) continue;
+    double r = S.b[S.gidx[D.row_off + i]];
+    for (int k = 0; k < K; ++k) {
+      const int64_t e = eb + (int64_t)k * D.npad + i;
+      r -= S.rval[e] * S.x[S.rcol[e]];
+    }
+    o += r * r;
+  }
+  block_sum2<128>(o, dummy, red);
+  if (threadIdx.x == 0) S.sub[it.p].part[0] = o;
+}
+
+// One CTA per item: x[O_p] = xalt[O_p] for systems whose result is in xalt.
+__global__ void __launch_bounds__(128) ras_copyback_kernel(Launch L) {
+  const Item it = L.items[blockIdx.x];
+  const SysDesc S = L.sys[it.sys];
+  if (!S.st->result_alt) return;
+  const SubDesc D = S.subs[it.p];
+  for (int t = threadIdx.x; t < D.n_own; t += 128) {
+    const int g = S.gidx[D.row_off + S.own_l[D.own_off + t]];
+    S.x[g] = S.xalt[g];
+  }
+}
+
+// --------------------------------------------------------------------------
+// local solvers
+// --------------------------------------------------------------------------
+
+// Banded Cholesky solve L L^T delta = r by warp 0. y[OFF + i] holds r on entry
+// and delta on exit; y[0, OFF) and y[OFF+npad, OFF+npad+W] must be zero.
+// Slabs stream through an NS-stage ring of shared memory with bulk copies
+// (cp.async.bulk + mbarrier), NS-1 blocks ahead of the block being solved.
+// gcount: running slab count of this CTA (selects stage and parity).
+template <typename T, typename CT, int NS>
+__device__ bool band_solve_warp(const T *slabF, const T *slabB, int nb, int W, CT *y, int OFF,
+                                CT *cbuf, T *ring, int ring_stride, uint64_t *mbar,
+                                uint32_t &gcount, int64_t timeout_ns) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t bytes = (uint32_t)((W + 1) * 32 * sizeof(T));
+  const int64_t slab = (int64_t)(W + 1) * 32;
+  bool ok = true;
+  for (int dir = 0; dir < 2; ++dir) {
+    const T *base = dir == 0 ? slabF : slabB;
+    // block processed at step s: forward K = s, backward K = nb-1-s
+    int issued = 0;
+    if (lane == 0) {
+      for (; issued < NS && issued < nb; ++issued) {
+        const int Kb = dir == 0 ? issued : nb - 1 - issued;
+        const uint32_t st = (gcount + issued) % NS;
+        fence_proxy_async();
+        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
+      }
+    }
+    issued = __shfl_sync(0xffffffffu, issued, 0);
+    int s = 0;
+    for (; s < nb; ++s) {
+      const uint32_t g = gcount + s;
+      const uint32_t st = g % NS;
+      const uint32_t par = (g / NS) & 1u;
+      if (!mbar_wait(&mbar[st], par, timeout_ns)) { ok = false; break; }
+      const T *sl = ring + st * ring_stride;
+      const int K = dir == 0 ? s : nb - 1 - s;
+      const int i = 32 * K + lane;
+      if (dir == 0) {
+        // c = r_K - L_{K,left} y_left
+        CT a0 = y[OFF + i], a1 = CT(0);
+        const CT *yb = y + OFF + i - W;
+        const int lim = W - lane;
+        int t = 0;
+        for (; t + 1 < lim; t += 2) {
+          a0 -= to_ct(sl[t * 32 + lane]) * yb[t];
+          a1 -= to_ct(sl[(t + 1) * 32 + lane]) * yb[t + 1];
+        }
+        if (t < lim) a0 -= to_ct(sl[t * 32 + lane]) * yb[t];
+        cbuf[lane] = a0 + a1;
+        __syncwarp();
+        CT v0 = CT(0), v1 = CT(0);
+        int e = 0;
+        for (; e + 1 <= lane; e += 2) {
+          v0 += to_ct(sl[(W - e) * 32 + lane]) * cbuf[lane - e];
+          v1 += to_ct(sl[(W - e - 1) * 32 + lane]) * cbuf[lane - e - 1];
+        }
+        if (e <= lane) v0 += to_ct(sl[(W - e) * 32 + lane]) * cbuf[lane - e];
+        y[OFF + i] = v0 + v1;
+      } else {
+        // c = y_K - U_{K,right} z_right
+        CT a0 = y[OFF + i], a1 = CT(0);
+        int d = 32 - lane;
+        for (; d + 1 <= W; d += 2) {
+          a0 -= to_ct(sl[d * 32 + lane]) * y[OFF + i + d];
+          a1 -= to_ct(sl[(d + 1) * 32 + lane]) * y[OFF + i + d + 1];
+        }
+        if (d <= W) a0 -= to_ct(sl[d * 32 + lane]) * y[OFF + i + d];
+        cbuf[lane] = a0 + a1;
+        __syncwarp();
+        CT v0 = CT(0), v1 = CT(0);
+        const int lim = 32 - lane;
+        int e = 0;
+        for (; e + 1 < lim; e += 2) {
+          v0 += to_ct(sl[e * 32 + lane]) * cbuf[lane + e];
+          v1 += to_ct(sl[(e + 1) * 32 + lane]) * cbuf[lane + e + 1];
+        }
+        if (e < lim) v0 += to_ct(sl[e * 32 + lane]) * cbuf[lane + e];
+        __syncwarp();
+        y[OFF + i] = v0 + v1;
+      }
+      __syncwarp();
+      // refill the stage just consumed
+      if (issued < nb) {
+        if (lane == 0) {
+          const int Kb = dir == 0 ? issued : nb - 1 - issued;
+          const uint32_t st2 = (gcount + issued) % NS;
+          fence_proxy_async();
+          tma_load_1d(ring + st2 * ring_stride, base + Kb * slab, bytes, &mbar[st2]);
+        }
+        ++issued;
+      }
+    }
+    if (!ok) {
+      // wait (bounded) for the copies still in flight before giving up
+      for (int s2 = s; s2 < issued; ++s2) {
+        const uint32_t g = gcount + s2;
+        mbar_wait(&mbar[g % NS], (g / NS) & 1u, timeout_ns);
+      }
+      gcount += issued;
+      return false;
+    }
+    gcount += nb;
+  }
+  return ok;
+}
+
+// m steps of textbook CG on A_p d = r from d = 0 (all threads). A_p in ELL
+// with local columns; vectors in shared memory.
+template <typename T, typename CT, int NT>
+__device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad, int m, CT *r,
+                         CT *p, CT *q, CT *d, CT *red) {
+  CT rr = CT(0);
+  for (int i = threadIdx.x; i < npad; i += NT) {
+    const CT v = i < n ? r[i] : CT(0);
+    r[i] = v;
+    p[i] = v;
+    d[i] = CT(0);
+    rr += v * v;
+  }
+  rr = block_sum<NT, CT>(rr, red);
+  for (int it = 0; it < m && rr != CT(0); ++it) {
+    CT pq = CT(0);
+    for (int i = threadIdx.x; i < n; i += NT) {
+      CT s = CT(0);
+      for (int k = 0; k < K; ++k) s += to_ct(lv[(int64_t)k * npad + i]) * p[lc[(int64_t)k * npad + i]];
+      q[i] = s;
+      pq += p[i] * s;
+    }
+    pq = block_sum<NT, CT>(pq, red);
+    const CT alpha = rr / pq;
+    CT rn = CT(0);
+    for (int i = threadIdx.x; i < n; i += NT) {
+      d[i] += alpha * p[i];
+      const CT ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      rn += ri * ri;
+    }
+    rn = block_sum<NT, CT>(rn, red);
+    const CT beta = rn / rr;
+    rr = rn;
+    for (int i = threadIdx.x; i < n; i += NT) p[i] = r[i] + beta * p[i];
+    __syncthreads();
+  }
+}
+
+// z = U^{-1} L^{-1} r with the ILU(0) factors, level by level.
+template <typename T, typename CT, int NT>
+__device__ __forceinline__ void ilu_apply(const int32_t *lc, const T *lu, int K, int npad,
+                                          const int32_t *lptr_f, int nlf, const int32_t *lrow_f,
+                                          const int32_t *lptr_b, int nlb, const int32_t *lrow_b,
+                                          const CT *r, CT *z) {
+  for (int lv = 0; lv < nlf; ++lv) {
+    const int a = lptr_f[lv], b = lptr_f[lv + 1];
+    for (int e = a + threadIdx.x; e < b; e += NT) {
+      const int i = lrow_f[e];
+      CT s = r[i];
+      for (int k = 0; k < K; ++k) {
+        const int c = lc[(int64_t)k * npad + i];
+        if (c < i) s -= to_ct(lu[(int64_t)k * npad + i]) * z[c];
+      }
+      z[i] = s;
+    }
+    __syncthreads();
+  }
+  for (int lv = 0; lv < nlb; ++lv) {
+    const int a = lptr_b[lv], b = lptr_b[lv + 1];
+    for (int e = a + threadIdx.x; e < b; e += NT) {
+      const int i = lrow_b[e];
+      CT s = z[i], dg = CT(1);
+      for (int k = 0; k < K; ++k) {
+        const int c = lc[(int64_t)k * npad + i];
+        const CT v = to_ct(lu[(int64_t)k * npad + i]);
+        if (c > i) s -= v * z[c];
+        else if (c == i && v != CT(0)) dg = v;  // zero-valued padding entries also use c == i
+      }
+      z[i] = s / dg;
+    }
+    __syncthreads();
+  }
+}
+
+// m steps of ILU(0)-preconditioned CG from d = 0 (all threads).
+template <typename T, typename CT, int NT>
+__device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *z, CT *p, CT *q,
+                          CT *d, CT *red) {
+  const int K = S.K, n = D.n, npad = D.npad;
+  const int32_t *lc = S.lcol + D.row_off * K;
+  const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
+  const T *lu = reinterpret_cast<const T *>(S.luval) + D.row_off * K;
+  const int32_t *lptr_f = S.lev_ptr + D.lev_off;
+  const int32_t *lptr_b = lptr_f + D.nlev_f + 1;
+  const int32_t *lrow_f = S.lev_rows + D.lrow_off;
+  const int32_t *lrow_b = lrow_f + n;
+  for (int i = threadIdx.x; i < npad; i += NT) {
+    if (i >= n) r[i] = CT(0);
+    z[i] = CT(0);
+    d[i] = CT(0);
+  }
+  __syncthreads();
+  ilu_apply<T, CT, NT>(lc, lu, K, npad, lptr_f, D.nlev_f, lrow_f, lptr_b, D.nlev_b, lrow_b, r, z);
+  CT rz = CT(0);
+  for (int i = threadIdx.x; i < npad; i += NT) {
+    p[i] = z[i];
+    rz += r[i] * z[i];
+  }
+  rz = block_sum<NT, CT>(rz, red);
+  for (int it = 0; it < m && rz != CT(0); ++it) {
+    CT pq = CT(0);
+    for (int i = threadIdx.x; i < n; i += NT) {
+      CT s = CT(0);
+      for (int k = 0; k < K; ++k) s += to_ct(lv[(int64_t)k * npad + i]) * p[lc[(int64_t)k * npad + i]];
+      q[i] = s;
+      pq += p[i] * s;
+    }
+    pq = block_sum<NT, CT>(pq, red);
+    const CT alpha = rz / pq;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      d[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    __syncthreads();
+    ilu_apply<T, CT, NT>(lc, lu, K, npad, lptr_f, D.nlev_f, lrow_f, lptr_b, D.nlev_b, lrow_b, r, z);
+    CT rn = CT(0);
+    for (int i = threadIdx.x; i < n; i += NT) rn += r[i] * z[i];
+    rn = block_sum<NT, CT>(rn, red);
+    const CT beta = rn / rz;
+    rz = rn;
+    for (int i = threadIdx.x; i < n; i += NT) p[i] = z[i] + beta * p[i];
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// the persistent RAS kernel
+// --------------------------------------------------------------------------
+
+constexpr int kBandStages = 3;
+
+template <int KIND, typename T, int NT>
+struct Smem {
+  using CT = typename CTypeOf<T>::type;
+  // band: ring | y | cbuf ; cg: r p q d ; ilu: r z p q d
+  static __host__ __device__ size_t ring_stride(int Wmax) {
+    const size_t b = (size_t)(Wmax + 1) * 32 * sizeof(T);
+    return ((b + 127) / 128) * 128 / sizeof(T);
+  }
+  static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
+  static __host__ __device__ size_t bytes(int Wmax, int npad_max) {
+    if (KIND == kBand) {
+      size_t b = kBandStages * ring_stride(Wmax) * sizeof(T);
+      b += ((size_t)(2 * Wmax + npad_max + 1 + 31) / 32 * 32) * sizeof(CT);
+      b += 32 * sizeof(CT);
+      return b;
+    }
+    const int nv = KIND == kCG ? 4 : 5;
+    return nv * vec_len(npad_max) * sizeof(CT);
+  }
+};
+
+template <int KIND, typename T, int NT>
+__global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
+  using CT = typename CTypeOf<T>::type;
+  using SM = Smem<KIND, T, NT>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ SysDesc s_sys;
+  __shared__ SubDesc s_sub;
+  __shared__ double s_red[NT / 32 * 2];
+  __shared__ CT s_redc[NT / 32];
+  __shared__ int s_flag[8];
+  __shared__ __align__(8) uint64_t s_mbar[kBandStages];
+  __shared__ int s_done[kMaxCtaSys];
+  __shared__ int64_t s_iter0[kMaxCtaSys];
+
+  const int tid = threadIdx.x;
+  const int c = blockIdx.x;
+  const int i0 = L.cta_off[c], i1 = L.cta_off[c + 1];
+  const int cs0 = L.cta_sys_off[c], cs1 = L.cta_sys_off[c + 1];
+  const int nls = cs1 - cs0;
+
+  // shared-memory carve-up
+  T *ring = nullptr;
+  CT *ybuf = nullptr, *cbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
+     *v4 = nullptr;
+  int ring_stride = 0;
+  const int OFF = L.Wmax;
+  if (KIND == kBand) {
+    ring_stride = (int)SM::ring_stride(L.Wmax);
+    ring = reinterpret_cast<T *>(smem);
+    ybuf = reinterpret_cast<CT *>(smem + kBandStages * ring_stride * sizeof(T));
+    cbuf = ybuf + (2 * L.Wmax + L.npad_max + 1 + 31) / 32 * 32;
+  } else {
+    const size_t vl = SM::vec_len(L.npad_max);
+    CT *base = reinterpret_cast<CT *>(smem);
+    v0 = base;
+    v1 = base + vl;
+    v2 = base + 2 * vl;
+    v3 = base + 3 * vl;
+    v4 = KIND == kILU ? base + 4 * vl : nullptr;
+  }
+  uint32_t gcount = 0;
+  if (KIND == kBand) {
+    if (tid == 0) {
+      for (int s = 0; s < kBandStages; ++s) mbar_init(&s_mbar[s], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  for (int k = tid; k < nls; k += NT) {
+    const int sys = L.cta_sys[2 * (cs0 + k)];
+    s_done[k] = 0;
+    s_iter0[k] = L.sys[sys].st->iters;
+  }
+  __syncthreads();
+
+  const bool async = L.mode == kAsync;
+  // wall-clock limit of the whole solve (each CTA measures from its own start)
+  const uint64_t t_start = gtimer();
+  auto past_deadline = [&]() -> bool {
+    return (int64_t)(gtimer() - t_start) > L.solve_limit_ns;
+  };
+
+  // ---- one local update of subdomain `it`: gather, solve, restricted update
+  // returns false on a device-side error (abort raised)
+  auto update = [&](double *xcur, double *xnext, double &res_loc, double &res_own) -> bool {
+    const SysDesc &S = s_sys;
+    const SubDesc &D = s_sub;
+    const int K = S.K;
+    const int64_t eb = D.row_off * K;
+    CT *rhs = KIND == kBand ? ybuf + OFF : v0;
+    if (KIND == kBand) {
+      // zero the halo of y (head and tail)
+      for (int e = tid; e < OFF; e += NT) ybuf[e] = CT(0);
+      for (int e = tid; e <= L.Wmax; e += NT) ybuf[OFF + D.npad + e] = CT(0);
+    }
+    double a_loc = 0.0, a_own = 0.0;
+    for (int i = tid; i < D.npad; i += NT) {
+      double r = 0.0;
+      if (i < D.n) {
+        r = S.b[S.gidx[D.row_off + i]];
+        for (int k = 0; k < K; ++k) {
+          const int64_t e = eb + (int64_t)k * D.npad + i;
+          const double xv = async ? ld_relaxed_f64(xcur + S.rcol[e]) : __ldcg(xcur + S.rcol[e]);
+          r -= S.rval[e] * xv;
+        }
+        a_loc += r * r;
+        if (S.ownf[D.row_off + i]) a_own += r * r;
+      }
+      rhs[i] = (CT)r;
+    }
+    block_sum2<NT>(a_loc, a_own, s_red);
+    res_loc = a_loc;
+    res_own = a_own;
+    // local solve
+    CT *delta = rhs;
+    if (KIND == kBand) {
+      bool ok = true;
+      if (tid < 32) {
+        const T *fac = reinterpret_cast<const T *>(S.fac);
+        const int64_t slab = (int64_t)(D.W + 1) * 32;
+        const int nb = D.npad / 32;
+        ok = band_solve_warp<T, CT, kBandStages>(fac + D.fac_off, fac + D.fac_off + nb * slab, nb,
+                                                 D.W, ybuf, OFF, cbuf, ring, ring_stride, s_mbar,
+                                                 gcount, L.timeout_ns);
+        if (!ok && tid == 0) set_error(L.ctl, kETIMEOUT, 2);
+        if (tid == 0) s_flag[4] = ok ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_flag[4]) return false;
+    } else if (KIND == kCG) {
+      const int32_t *lc = S.lcol + D.row_off * K;
+      const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
+      __syncthreads();
+      cg_solve<T, CT, NT>(lc, lv, K, D.n, D.npad, L.m, v0, v1, v2, v3, s_redc);
+      delta = v3;
+    } else {
+      __syncthreads();
+      pcg_solve<T, CT, NT>(S, D, L.m, v0, v1, v2, v3, v4, s_redc);
+      delta = v4;
+    }
+    // restricted prolongation: only owned rows are written (RAS)
+    const int32_t *own = S.own_l + D.own_off;
+    for (int t = tid; t < D.n_own; t += NT) {
+      const int i = own[t];
+      const int g = S.gidx[D.row_off + i];
+      if (async) {
+        st_relaxed_f64(xnext + g, ld_relaxed_f64(xcur + g) + (double)delta[i]);
+      } else {
+        __stcg(xnext + g, __ldcg(xcur + g) + (double)delta[i]);
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
+  auto load_item = [&](int it) {
+    __syncthreads();  // everyone is done with the previous item's shared state
+    if (tid == 0) {
+      const Item item = L.items[it];
+      s_sys = L.sys[item.sys];
+      s_sub = s_sys.subs[item.p];
+      s_flag[5] = item.p;
+      s_flag[6] = item.ls;
+    }
+    __syncthreads();
+  };
+
+  if (!async) {
+    // ------------------------------------------------------------ SYNC
+    int fin = 0;
+    for (int64_t j = 0; j < L.step_limit; ++j) {
+      for (int it = i0; it < i1; ++it) {
+        load_item(it);
+        if (s_done[s_flag[6]]) continue;
+        const int p = s_flag[5];
+        double *xc = (j & 1) ? s_sys.xalt : s_sys.x;
+        double *xn = (j & 1) ? s_sys.x : s_sys.xalt;
+        double rl, ro;
+        if (!update(xc, xn, rl, ro)) goto out;
+        if (tid == 0) {
+          SubState &ss = s_sys.sub[p];
+          ss.part[j & 1] = ro;
+          ss.updates += 1;
+        }
+      }
+      if (tid == 0 && past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
+      if (!grid_barrier(L.ctl, fin, L.timeout_ns, s_flag)) goto out;
+      fin = 0;
+      if (s_flag[1] <= 0) break;  // every system decided before this barrier
+      // decisions for iteration j (residual of x^j)
+      for (int k = 0; k < nls; ++k) {
+        if (s_done[k]) continue;
+        const int sys = L.cta_sys[2 * (cs0 + k)];
+        const int lead = L.cta_sys[2 * (cs0 + k) + 1];
+        if (tid < 32) {
+          const SysDesc &S = L.sys[sys];
+          const double res2 = warp_sum_partials(S.sub, S.P, (int)(j & 1), true);
+          if (tid == 0) {
+            const int64_t kk = s_iter0[k] + j;
+            const bool conv = res2 < S.tol2 * S.st->b2 || res2 == 0.0;
+            int done = 0;
+            if (conv) {
+              done = 1;
+              if (lead) {
+                S.st->iters = kk;
+                S.st->res2 = res2;
+                S.st->status = kOK;
+                S.st->result_alt = (int)(j & 1);
+                S.st->done = 1;
+              }
+            } else if (kk + 1 >= L.max_updates || j + 1 == L.step_limit) {
+              if (kk + 1 >= L.max_updates) done = 1;
+              if (lead) {
+                S.st->iters = kk + 1;
+                S.st->res2 = res2;
+                S.st->status = done ? kENOCONV : kOK;
+                S.st->result_alt = (int)((j + 1) & 1);
+                S.st->done = done;
+              }
+            }
+            if (done) {
+              s_done[k] = 1;
+              if (lead) fin++;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    // ----------------------------------------------------------- ASYNC
+    uint64_t t_idle = gtimer();
+    for (;;) {
+      int any_work = 0, all_done = 1;
+      for (int it = i0; it < i1; ++it) {
+        load_item(it);
+        const int p = s_flag[5];
+        SubState &ss = s_sys.sub[p];
+        SysState *st = s_sys.st;
+        if (tid == 0) {
+          const uint32_t wd = ld_acquire_u32(&st->word);
+          int action = 0;  // 0 none, 1 update, 2 park, 3 check
+          const int phase = (int)(wd & 3u);
+          const int epoch = (int)(wd >> 2);
+          if (ld_relaxed_s32(&L.ctl->abort)) action = -1;
+          else if (phase != kDone) {
+            s_flag[3] = 0;
+            if (phase == kRun) {
+              if (ss.updates >= L.max_updates) {
+                st->status = kENOCONV;
+                atomicCAS(&st->word, wd, ((uint32_t)epoch << 2) | kDone);
+              } else if (ss.step_updates < L.step_limit) {
+                action = 1;
+              }
+            } else if (phase == kDrain) {
+              if (ss.park_epoch != epoch) action = 2;
+            } else {
+              if (ss.check_epoch != epoch) action = 3;
+            }
+          }
+          s_flag[0] = action;
+          s_flag[1] = (int)wd;
+          s_flag[2] = (phase != kDone) ? 1 : 0;
+        }
+        __syncthreads();
+        const int action = s_flag[0];
+        const uint32_t wd = (uint32_t)s_flag[1];
+        if (action < 0) goto out;
+        if (s_flag[2]) all_done = 0;
+        if (action == 0) continue;
+        any_work = 1;
+        const int epoch = (int)(wd >> 2);
+        if (action == 1) {
+          // acquire the neighbours' published versions before reading x
+          if (tid == 0) {
+            uint64_t seen = 0;
+            const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+            for (int q = 0; q < s_sub.n_nbr; ++q) seen += ld_acquire_u32(&s_sys.sub[nb[q]].version);
+            if (ss.updates > 0 && seen == ss.nbr_seen) ss.stale += 1;
+            ss.nbr_seen = seen;
+          }
+          __syncthreads();
+          double rl, ro;
+          if (!update(s_sys.x, s_sys.x, rl, ro)) goto out;
+          if (tid == 0) {
+            __threadfence();
+            ss.updates += 1;
+            ss.step_updates += 1;
+            st_release_u32(&ss.version, (uint32_t)ss.updates);
+            // local criterion (Eq. 2) on the residual gathered before the update
+            const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
+            if (conv && ss.conv_epoch != epoch) {
+              ss.conv_epoch = epoch;
+              const int nc = atomicAdd(&st->nconv, 1) + 1;
+              if (nc == s_sys.P) atomicCAS(&st->word, ((uint32_t)epoch << 2) | kRun,
+                                           ((uint32_t)epoch << 2) | kDrain);
+            } else if (!conv && ss.conv_epoch == epoch) {
+              ss.conv_epoch = -1;
+              atomicSub(&st->nconv, 1);
+            }
+          }
+        } else if (action == 2) {
+          if (tid == 0) {
+            ss.park_epoch = epoch;
+            __threadfence();
+            const int np = atomicAdd(&st->nparked, 1) + 1;
+            if (np == s_sys.P) {
+              __threadfence();
+              st_release_u32(&st->word, ((uint32_t)epoch << 2) | kCheck);
+            }
+          }
+        } else {
+          // post-termination check: owned residual of the (now frozen) x
+          const SysDesc &S = s_sys;
+          const SubDesc &D = s_sub;
+          const int K = S.K;
+          const int64_t eb = D.row_off * K;
+          double o = 0.0, dmy = 0.0;
+          for (int i = tid; i < D.n; i += NT) {
+            if (!S.ownf[D.row_off + i]) continue;
+            double r = S.b[S.gidx[D.row_off + i]];
+            for (int k = 0; k < K; ++k) {
+              const int64_t e = eb + (int64_t)k * D.npad + i;
+              r -= S.rval[e] * ld_relaxed_f64(S.x + S.rcol[e]);
+            }
+            o += r * r;
+          }
+          block_sum2<NT>(o, dmy, s_red);
+          if (tid < 32) {
+            int last = 0;
+            if (tid == 0) {
+              st_relaxed_f64(&ss.part[0], o);
+              ss.check_epoch = epoch;
+              __threadfence();
+              last = (atomicAdd(&st->nchecked, 1) + 1 == S.P) ? 1 : 0;
+              if (last) __threadfence();
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+              const double res2 = warp_sum_partials(S.sub, S.P, 0, true);
+              if (tid == 0) {
+                st->res2 = res2;
+                uint32_t nw;
+                if (res2 < S.tol2 * st->b2 || res2 == 0.0) {
+                  st->status = kOK;
+                  nw = ((uint32_t)epoch << 2) | kDone;
+                } else if (ld_relaxed_s32(&st->restarts) >= L.max_restarts) {
+                  st->status = kENOCONV;
+                  nw = ((uint32_t)epoch << 2) | kDone;
+                } else {
+                  st->restarts += 1;
+                  st->nconv = 0;
+                  st->nparked = 0;
+                  st->nchecked = 0;
+                  nw = ((uint32_t)(epoch + 1) << 2) | kRun;
+                }
+                __threadfence();
+                st_release_u32(&st->word, nw);
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (all_done) break;
+      if (tid == 0 && past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
+      if (any_work) {
+        t_idle = gtimer();
+      } else {
+        if (!L.persist) break;
+        if ((int64_t)(gtimer() - t_idle) > L.timeout_ns) {
+          if (tid == 0) set_error(L.ctl, kETIMEOUT, 3);
+          break;
+        }
+        __nanosleep(500);
+      }
+    }
+  }
+out:
+  return;
+}
+
+// --------------------------------------------------------------------------
+// host-side launchers
+// --------------------------------------------------------------------------
+
+template <int KIND, typename T, int NT>
+static cudaError_t launch_main_t(const Launch &L, int grid, size_t smem, cudaStream_t stream) {
+  auto fn = ras_main_kernel<KIND, T, NT>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  Launch Lc = L;
+  void *args[] = {&Lc};
+  return cudaLaunchCooperativeKernel((void *)fn, dim3(grid), dim3(NT), args, smem, stream);
+}
+
+template <int KIND, typename T, int NT>
+static int occupancy_t(size_t smem) {
+  auto fn = ras_main_kernel<KIND, T, NT>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+#define RAS_DISPATCH(KIND_, PREC_, NT_, CALL)                                              \
+  do {                                                                                     \
+    if (KIND_ == kBand) {                                                                  \
+      if (PREC_ == kF64) { CALL(kBand, double, 128); }                                     \
+      else if (PREC_ == kF32) { CALL(kBand, float, 128); }                                 \
+      else { CALL(kBand, __nv_bfloat16, 128); }                                            \
+    } else if (KIND_ == kCG) {                                                             \
+      if (PREC_ == kF64) { if (NT_ == 512) { CALL(kCG, double, 512); } else { CALL(kCG, double, 256); } } \
+      else { if (NT_ == 512) { CALL(kCG, float, 512); } else { CALL(kCG, float, 256); } }  \
+    } else {                                                                               \
+      if (PREC_ == kF64) { if (NT_ == 512) { CALL(kILU, double, 512); } else { CALL(kILU, double, 256); } } \
+      else { if (NT_ == 512) { CALL(kILU, float, 512); } else { CALL(kILU, float, 256); } } \
+    }                                                                                      \
+  } while (0)
+
+size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max) {
+  size_t r = 0;
+#define RAS_SMEM(K_, T_, NT_) r = Smem<K_, T_, NT_>::bytes(Wmax, npad_max)
+  RAS_DISPATCH(kind, prec, nt, RAS_SMEM);
+#undef RAS_SMEM
+  return r;
+}
+
+int main_threads(int kind, int nt_pref) {
+  if (kind == kBand) return 128;
+  return nt_pref == 512 ? 512 : 256;
+}
+
+int main_occupancy(int kind, int prec, int nt, size_t smem) {
+  int r = 0;
+#define RAS_OCC(K_, T_, NT_) r = occupancy_t<K_, T_, NT_>(smem)
+  RAS_DISPATCH(kind, prec, nt, RAS_OCC);
+#undef RAS_OCC
+  return r;
+}
+
+cudaError_t launch_main(int kind, int prec, int nt, const Launch &L, int grid, size_t smem,
+                        cudaStream_t stream) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define RAS_LAUNCH(K_, T_, NT_) e = launch_main_t<K_, T_, NT_>(L, grid, smem, stream)
+  RAS_DISPATCH(kind, prec, nt, RAS_LAUNCH);
+#undef RAS_LAUNCH
+  return e;
+}
+
+cudaError_t launch_init(const Launch &L, int nitems, cudaStream_t stream) {
+  ras_init_kernel<<<nitems, 128, 0, stream>>>(L);
+  ras_sysnorm_kernel<<<L.nsys, 32, 0, stream>>>(L, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Launch &L, int nitems, cudaStream_t stream) {
+  ras_residual_kernel<<<nitems, 128, 0, stream>>>(L);
+  ras_sysnorm_kernel<<<L.nsys, 32, 0, stream>>>(L, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copyback(const Launch &L, int nitems, cudaStream_t stream) {
+  ras_copyback_kernel<<<nitems, 128, 0, stream>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_chol(const BandJob *jobs, int njobs, int max_w, double *band,
+                             GridCtl *ctl, cudaStream_t stream) {
+  const size_t smem = (size_t)(max_w + 1) * (max_w + 1) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(band_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  band_chol_kernel<<<njobs, 256, smem, stream>>>(jobs, band, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_layout(int prec, const LayoutJob *jobs, int njobs, const double *band,
+                               void *fac, cudaStream_t stream) {
+  if (prec == kF64)
+    band_layout_kernel<double><<<njobs, 32, 0, stream>>>(jobs, band, (double *)fac);
+  else if (prec == kF32)
+    band_layout_kernel<float><<<njobs, 32, 0, stream>>>(jobs, band, (float *)fac);
+  else
+    band_layout_kernel<__nv_bfloat16><<<njobs, 32, 0, stream>>>(jobs, band, (__nv_bfloat16 *)fac);
+  return cudaGetLastError();
+}
+
+}  // namespace ras

@@ -1,0 +1,268 @@
+"""GPU parity tests: the CUDA path through the C ABI against the CPU oracle.
+
+Bars (stated per test): index maps and partitions bit-exact; synchronous
+FP64 iterates x^k equal to the oracle's up to rounding (1e-12 relative for
+the banded direct solver, 1e-9 for CG / ILU-PCG whose dot products are
+reduced in a different order); every converged result has a true FP64
+relative residual below the tolerance (checked with the oracle's residual)
+and an error against the direct solution within the bound the residual
+implies."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import oracle
+import paper_2003_05361_gb300 as ras
+import problems
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+BAND, CG, ILU = ras.RAS_LOCAL_BANDCHOL, ras.RAS_LOCAL_CG, ras.RAS_LOCAL_ILU0_CG
+F64, F32, BF16 = ras.RAS_FP64, ras.RAS_FP32, ras.RAS_BF16_STORE
+OR_KIND = {BAND: oracle.BANDCHOL, CG: oracle.CG, ILU: oracle.ILU0_CG}
+OR_PREC = {F64: oracle.FP64, F32: oracle.FP32, BF16: oracle.BF16}
+
+
+def gpu_solve(A, b, part, P, gamma, kind=BAND, prec=F64, m=20, mode=ras.RAS_SYNC, tol=1e-8,
+              max_updates=0, x0=None, ctx=None):
+    own = ctx is None
+    if own:
+        ctx = ras.ras_setup(A, part, P, gamma, kind, prec, m)
+    bd = torch.tensor(b, device="cuda")
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda") if x0 is None else \
+        torch.tensor(x0, device="cuda")
+    info = ras.ras_solve(ctx, bd, x, tol, mode, max_updates)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    if own:
+        ras.ras_destroy(ctx)
+    return xh, info
+
+
+def true_relres(A, b, x):
+    _, rn = oracle.residual(A, b, x)
+    return rn / np.linalg.norm(b)
+
+
+# ---------------------------------------------------------------- maps
+
+@pytest.mark.parametrize("case,gamma", [("2d", 0), ("2d", 1), ("2d", 2), ("2d", 4),
+                                        ("3d_bfs", 1), ("3d_bfs", 2), ("diff_bfs", 3)])
+def test_maps_bit_exact(case, gamma):
+    if case == "2d":
+        A, P = problems.poisson2d(20), 6
+        part = ras.ras_partition_regular2d(20, 20, 3, 2)
+    elif case == "3d_bfs":
+        A, P = problems.poisson3d(8), 5
+        part = ras.ras_partition_bfs(A, P, 3)
+    else:
+        A, P = problems.diffusion2d(30, problems.grf_coefficient(30, 4)), 7
+        part = ras.ras_partition_bfs(A, P, 1)
+    ctx = ras.ras_setup(A, part, P, gamma, CG, F64, 5)
+    for p in range(P):
+        om, ow, ifc = ras.ras_get_maps(ctx, p)
+        om2, ow2, ifc2 = oracle.overlap(A, part, P, p, gamma)
+        assert np.array_equal(om, om2) and np.array_equal(ow, ow2) and np.array_equal(ifc, ifc2)
+    ras.ras_destroy(ctx)
+
+
+# ---------------------------------------------------------------- sync FP64
+
+def test_config1_sync_band_fp64():
+    # 128^2 Poisson, eigenvector RHS, regular 2x2, overlap 2, banded Cholesky
+    N = 128
+    A = problems.poisson2d(N)
+    b, u, lam = problems.rhs_eigen2d(N)
+    part = ras.ras_partition_regular2d(N, N, 2, 2)
+    x, info = gpu_solve(A, b, part, 4, 2)
+    xo, it, hist = oracle.ras_sync(A, b, part, 4, 2, tol=1e-8)
+    assert info.status == 0
+    assert abs(info.iterations - it) <= 1
+    assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+    rr = true_relres(A, b, x)
+    assert rr < 1e-8 and abs(rr - info.relres) <= 1e-6 * rr
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= rr * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("kind,m,rtol", [(BAND, 0, 1e-12), (CG, 8, 1e-9), (ILU, 4, 1e-9)])
+def test_sync_trajectory_matches_oracle(kind, m, rtol):
+    # ragged grid: 45 = 15*3, 40 rows split in 2; several 32-row tiles per subdomain
+    NX = 45
+    A = problems.poisson2d(NX)
+    b = problems.rhs_uniform(A.n, 11)
+    part = ras.ras_partition_regular2d(NX, NX, 3, 2)
+    ctx = ras.ras_setup(A, part, 6, 2, kind, F64, max(m, 1))
+    for k in (1, 2, 5):
+        x, info = gpu_solve(A, b, part, 6, 2, kind, F64, m, max_updates=k, ctx=ctx)
+        assert info.status == ras.RAS_ENOCONV and info.iterations == k
+        xo, _ = oracle.ras_sync(A, b, part, 6, 2, OR_KIND[kind], oracle.FP64, max(m, 1), tol=0.0,
+                                max_iter=k, allow_noconv=True)[:2]
+        assert np.linalg.norm(x - xo) <= rtol * np.linalg.norm(xo), k
+    ras.ras_destroy(ctx)
+
+
+@pytest.mark.parametrize("kind", [BAND, CG, ILU])
+def test_sync_converged_matches_oracle(kind):
+    N = 60
+    A = problems.diffusion2d(N, problems.grf_coefficient(N, 4))
+    b = problems.rhs_uniform(A.n, 4)
+    part = ras.ras_partition_bfs(A, 5, 2)
+    x, info = gpu_solve(A, b, part, 5, 3, kind, F64, 10)
+    xo, it, _ = oracle.ras_sync(A, b, part, 5, 3, OR_KIND[kind], oracle.FP64, 10, tol=1e-8)
+    # CG / PCG make the outer iteration non-linear in x: a different rounding
+    # order (tree reductions, FMA) shifts where a slow run crosses the
+    # threshold; FMA contraction alone moves the oracle's own count by 2 here
+    slack = 1 if kind == BAND else max(2, int(0.01 * it))
+    assert info.status == 0 and abs(info.iterations - it) <= slack
+    assert true_relres(A, b, x) < 1e-8
+    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+# ---------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("kind,prec", [(BAND, F32), (BAND, BF16), (CG, F32), (ILU, F32)])
+def test_mixed_precision_reaches_fp64_accuracy(kind, prec):
+    N = 64
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 1)
+    part = ras.ras_partition_regular2d(N, N, 2, 2)
+    x, info = gpu_solve(A, b, part, 4, 2, kind, prec, 10, tol=1e-10)
+    assert info.status == 0
+    rr = true_relres(A, b, x)
+    assert rr < 1e-10
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-7
+    _, it, _ = oracle.ras_sync(A, b, part, 4, 2, OR_KIND[kind], OR_PREC[prec], 10, tol=1e-10)
+    assert abs(info.iterations - it) <= max(3, 0.1 * it)
+
+
+# ---------------------------------------------------------------- async
+
+@pytest.mark.parametrize("kind,prec", [(BAND, F64), (BAND, F32), (CG, F64), (ILU, F32)])
+def test_async_converges_to_oracle_solution(kind, prec):
+    N = 64
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 2)
+    part = ras.ras_partition_regular2d(N, N, 4, 4)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    ctx = ras.ras_setup(A, part, 16, 2, kind, prec, 10)
+    for rep in range(3):
+        x, info = gpu_solve(A, b, part, 16, 2, kind, prec, 10, mode=ras.RAS_ASYNC, tol=1e-9, ctx=ctx)
+        assert info.status == 0, info.as_dict()
+        rr = true_relres(A, b, x)
+        assert rr < 1e-9
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
+        assert info.updates_min >= 1 and info.updates_max >= info.updates_median >= info.updates_min
+    ras.ras_destroy(ctx)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_single_subdomain_one_iteration():
+    A = problems.poisson2d(30)
+    b = problems.rhs_uniform(A.n, 3)
+    x, info = gpu_solve(A, b, np.zeros(A.n, np.int32), 1, 2)
+    assert info.status == 0 and info.iterations == 1
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_exact_initial_guess_zero_iterations():
+    A = problems.poisson2d(20)
+    b = problems.rhs_uniform(A.n, 3)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    part = ras.ras_partition_regular2d(20, 20, 2, 2)
+    for mode in (ras.RAS_SYNC, ras.RAS_ASYNC):
+        x, info = gpu_solve(A, b, part, 4, 1, mode=mode, tol=1e-6, x0=xs)
+        assert info.status == 0
+        if mode == ras.RAS_SYNC:
+            assert info.iterations == 0 and np.array_equal(x, xs)
+
+
+def test_zero_rhs():
+    A = problems.poisson2d(12)
+    b = np.zeros(A.n)
+    part = ras.ras_partition_regular2d(12, 12, 2, 2)
+    for mode in (ras.RAS_SYNC, ras.RAS_ASYNC):
+        x, info = gpu_solve(A, b, part, 4, 1, mode=mode)
+        assert info.status == 0 and np.all(x == 0)
+
+
+def test_tiny_subdomains_and_zero_overlap():
+    # 4-point subdomains (n_p < 32: one padded tile), overlap 0 = block Jacobi
+    N = 6
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 5)
+    part = ras.ras_partition_regular2d(N, N, 3, 3)
+    for gamma in (0, 1):
+        x, info = gpu_solve(A, b, part, 9, gamma, tol=1e-10)
+        xo, it, _ = oracle.ras_sync(A, b, part, 9, gamma, tol=1e-10)
+        assert info.status == 0 and abs(info.iterations - it) <= 1
+        assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_max_updates_reports_noconv():
+    A = problems.poisson2d(40)
+    b = problems.rhs_uniform(A.n, 1)
+    part = ras.ras_partition_regular2d(40, 40, 4, 4)
+    x, info = gpu_solve(A, b, part, 16, 1, mode=ras.RAS_ASYNC, max_updates=3)
+    assert info.status == ras.RAS_ENOCONV
+    assert info.updates_max <= 3
+
+
+# ---------------------------------------------------------------- batch
+
+def test_batch_equals_solo_sync_bitwise():
+    sizes = [(40, 2, 2), (64, 2, 3), (33, 3, 1)]
+    ctxs, bs, xs, solo = [], [], [], []
+    for N, px, py in sizes:
+        A = problems.poisson2d(N)
+        b = problems.rhs_uniform(A.n, N)
+        part = ras.ras_partition_regular2d(N, N, px, py)
+        ctx = ras.ras_setup(A, part, px * py, 2, BAND, F64)
+        x1, info1 = gpu_solve(A, b, part, px * py, 2, ctx=ctx)
+        solo.append((x1, info1.iterations))
+        ctxs.append(ctx)
+        bs.append(torch.tensor(b, device="cuda"))
+        xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+    infos = ras.ras_solve_batch(ctxs, bs, xs, 1e-8, ras.RAS_SYNC)
+    for (x1, it1), x, info in zip(solo, xs, infos):
+        assert info.status == 0 and info.iterations == it1
+        assert np.array_equal(x.cpu().numpy(), x1)
+    for c in ctxs:
+        ras.ras_destroy(c)
+
+
+def test_batch_async():
+    ctxs, bs, xs, probs = [], [], [], []
+    for N in (48, 64, 80):
+        A = problems.poisson2d(N)
+        b = problems.rhs_uniform(A.n, N)
+        part = ras.ras_partition_regular2d(N, N, 2, 2)
+        ctxs.append(ras.ras_setup(A, part, 4, 2, BAND, F32))
+        bs.append(torch.tensor(b, device="cuda"))
+        xs.append(torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+        probs.append((A, b))
+    infos = ras.ras_solve_batch(ctxs, bs, xs, 1e-9, ras.RAS_ASYNC)
+    for (A, b), x, info in zip(probs, xs, infos):
+        assert info.status == 0
+        assert true_relres(A, b, x.cpu().numpy()) < 1e-9
+    for c in ctxs:
+        ras.ras_destroy(c)
+
+
+def test_host_buffers_entry_point():
+    N = 50
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 8)
+    part = ras.ras_partition_regular2d(N, N, 2, 2)
+    ctx = ras.ras_setup(A, part, 4, 2, BAND, F64)
+    x = np.zeros(A.n)
+    info = ras.ras_solve_host(ctx, b, x, 1e-8, ras.RAS_SYNC)
+    xd, info2 = gpu_solve(A, b, part, 4, 2, ctx=ctx)
+    assert info.status == 0 and np.array_equal(x, xd)
+    assert abs(ras.ras_relres(ctx, torch.tensor(b, device="cuda"), torch.tensor(x, device="cuda"))
+               - true_relres(A, b, x)) < 1e-12
+    ras.ras_destroy(ctx)
