@@ -1,0 +1,430 @@
+"""Benchmark: time-to-solution of asynchronous vs synchronous RAS on one GB300.
+
+Workload (one step = one full solve to relative residual 1e-8, inputs resident
+in HBM): 2D Poisson 5-point on a 1024 x 1024 grid (1,048,576 unknowns), b
+uniform in [-1, 1] from SplitMix64 seed 1, regular2d 16 x 16 = 256 subdomains,
+overlap 4, local CG with 20 steps per update. The headline `value` is the
+asynchronous mixed-precision solver (FP32 local CG, FP64 residual / update /
+convergence tests); the plain synchronous FP64 solver and the other variants
+are reported beside it.
+
+--impl reference runs the CPU oracle (sequential FP64 synchronous RAS with the
+same local solver) on the host cores: each step is a bounded sample of
+iterations, extrapolated to the oracle's iteration count for this workload
+(tests/golden/config2_sync_fp64_cg20_iterations.txt, written by the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import problems  # noqa: E402
+
+METRIC = ("time-to-solution at rel. residual 1e-8 & HBM GB/s: async vs sync RAS; "
+          "serving p50/p99")
+N_GRID, PX, GAMMA, M_INNER, TOL, SEED = 1024, 16, 4, 20, 1e-8, 1
+WORKLOAD = ("2D Poisson 5-point 1024x1024 (1,048,576 unknowns), uniform RHS seed 1, "
+            "regular2d 16x16 = 256 subdomains, overlap 4, local CG 20 steps")
+GOLDEN_ITERS = os.path.join(ROOT, "tests", "golden", "config2_sync_fp64_cg20_iterations.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2003_05361_gb300", "csrc", "ras_kernels.cu")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def problem():
+    A = problems.poisson2d(N_GRID)
+    b = problems.rhs_uniform(A.n, SEED)
+    return A, b
+
+
+def oracle_iterations():
+    with open(GOLDEN_ITERS) as f:
+        return int([ln for ln in f if ln.strip() and not ln.startswith("#")][0])
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(A, b, part, budget_s: float, nthreads: int):
+    """Times the oracle's sync RAS on a bounded number of iterations; returns
+    (seconds per iteration, iterations run)."""
+    import oracle
+
+    k = 1
+    t0 = time.perf_counter()
+    oracle.ras_sync(A, b, part, PX * PX, GAMMA, oracle.CG, oracle.FP64, M_INNER, tol=0.0,
+                    max_iter=k, nthreads=nthreads, allow_noconv=True)
+    t1 = time.perf_counter() - t0
+    k2 = max(1, int(budget_s / max(t1, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    oracle.ras_sync(A, b, part, PX * PX, GAMMA, oracle.CG, oracle.FP64, M_INNER, tol=0.0,
+                    max_iter=k2, nthreads=nthreads, allow_noconv=True)
+    t2 = time.perf_counter() - t0
+    return (t1 + t2) / (k + k2), k + k2
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    import oracle
+
+    A, b = problem()
+    part = oracle.partition_regular2d(N_GRID, N_GRID, PX, PX)
+    iters = oracle_iterations()
+    cores = os.cpu_count() or 1
+    budget = float(os.environ.get("RAS_REF_STEP_S", "8"))
+    for _ in range(args.warmup):
+        oracle_sample(A, b, part, budget / 4, cores)
+    vals, samples = [], []
+    for _ in range(args.steps):
+        spi, k = oracle_sample(A, b, part, budget, cores)
+        vals.append(spi * iters * 1e3)
+        samples.append(k)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": "sync", "local_solver": "CG-20",
+                   "local_precision": "fp64", "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": f"{statistics.median(samples)} sync RAS iterations per step, "
+                                   f"extrapolated to the oracle's {iters} iterations"},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.out:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline model
+
+def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m):
+    """Algorithmic bytes of one local update of each subdomain:
+    residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p,
+    local CG = nnz(A_p) (s_v + 2) m (matrix re-read every step),
+    band = 2 n_p (w_p + 1) s_f, update = 8 |O_p| written."""
+    rp, ci = A.row_ptr, A.col
+    rownnz = np.diff(rp)
+    out = []
+    for p in range(ctx.num_parts):
+        om, ow, ifc = ras.ras_get_maps(ctx, p)
+        n_p, e_p, o_p = om.size, ifc.size, int(ow.sum())
+        nnz_rows = int(rownnz[om].sum())
+        inside = np.zeros(A.n, bool)
+        inside[om] = True
+        # nnz(A_p): entries of Omega_p's rows whose column lies in Omega_p
+        starts, ends = rp[om], rp[om + 1]
+        idx = np.concatenate([np.arange(s, e) for s, e in zip(starts, ends)])
+        nnz_p = int(inside[ci[idx]].sum())
+        res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
+        if kind == ras.RAS_LOCAL_CG:
+            loc = nnz_p * (prec_bytes + 2) * m
+        else:
+            loc = 0
+        out.append(res + loc + 8 * o_p)
+    return np.array(out, dtype=np.float64)
+
+
+def profile_traffic(variant: str):
+    """DRAM bytes per local update of the persistent kernel from a committed
+    ncu summary (profiles/*.txt) taken on the current kernel source and the
+    same variant; None when there is none."""
+    import glob
+
+    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.txt"))):
+        kv = {}
+        for ln in open(path):
+            if ":" in ln and not ln.startswith((" ", "#")):
+                k, v = ln.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_src_sha256_16") == src_hash and kv.get("variant") == variant:
+            try:
+                return float(kv["dram_bytes_per_update"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    A, b = problem()
+    part = ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX)
+    bd = torch.tensor(b, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    variants = {
+        "async_fp32": (ras.RAS_ASYNC, ras.RAS_FP32),
+        "sync_fp64": (ras.RAS_SYNC, ras.RAS_FP64),
+        "async_fp64": (ras.RAS_ASYNC, ras.RAS_FP64),
+        "sync_fp32": (ras.RAS_SYNC, ras.RAS_FP32),
+    }
+    ctxs = {p: ras.ras_setup(A, part, PX * PX, GAMMA, ras.RAS_LOCAL_CG, p, M_INNER, stream=stream)
+            for p in (ras.RAS_FP32, ras.RAS_FP64)}
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    def solve(mode, prec):
+        x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        flush.fill_(1.0)  # L2 flush outside the timed region
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = ras.ras_solve(ctxs[prec], bd, x, TOL, mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if info.status != 0:
+            raise RuntimeError(f"solve failed: {info.as_dict()}")
+        return e0.elapsed_time(e1), info, x
+
+    head_mode, head_prec = variants["async_fp32"]
+    for _ in range(args.warmup):
+        solve(head_mode, head_prec)
+    barrier()
+    torch.cuda.synchronize()
+    times, infos = [], []
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            t, info, x = solve(head_mode, head_prec)
+            times.append(t)
+            infos.append(info)
+    barrier()
+    t_step = max(times) if world == 1 else max(times)
+    med = statistics.median(times)
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([med], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        med = float(tt.item())
+
+    # relative residual of the last result (FP64 on the device)
+    relres = ras.ras_relres(ctxs[head_prec], bd, x)
+
+    # other variants, one solve each
+    var_out = {}
+    if not args.quick:
+        for name, (mode, prec) in variants.items():
+            if name == "async_fp32":
+                continue
+            t, info, _ = solve(mode, prec)
+            var_out[name] = {"ms": t, "iterations": info.iterations,
+                             "updates_median": info.updates_median, "relres": info.relres,
+                             "kernel_ms": info.kernel_ms}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.quick:
+        bh = torch.tensor(b).pin_memory()
+        e2e_t = []
+        for _ in range(args.steps):
+            xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info_h = ras.ras_solve_host(ctxs[head_prec], bh, xh, TOL, head_mode)
+            e2e_t.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": statistics.median(e2e_t), "unit": "ms",
+               "h2d_bytes_per_step": 2 * 8 * A.n, "d2h_bytes_per_step": 8 * A.n}
+
+    # roofline of the persistent kernel
+    info = infos[len(infos) // 2]
+    counts = ras.ras_get_update_counts(ctxs[head_prec])
+    per_upd = subdomain_bytes(A, ras, ctxs[head_prec], ras.RAS_LOCAL_CG, 4, M_INNER)
+    alg_bytes = float(np.dot(counts, per_upd))
+    kernel_s = info.kernel_ms / 1e3
+    achieved = alg_bytes / kernel_s / 1e9
+    peak, peak_src = measured_peaks()
+    tpu = profile_traffic("async_fp32")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": (tpu * float(counts.sum())) if tpu else None,
+            "kernel": "ras_main_kernel<CG, float, 256>", "kernel_ms": info.kernel_ms,
+            "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
+
+    launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)
+    line = {
+        "metric": METRIC, "value": med, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": med, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mode": "async", "local_solver": "CG-20",
+                   "local_precision": "fp32", "outer_precision": "fp64", "tol": TOL,
+                   "l2": "flushed before every step (256 MB write); working set 0.2 GB > L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iterations_median_updates": info.updates_median,
+        "updates": {"min": info.updates_min, "median": info.updates_median,
+                    "max": info.updates_max, "stale": info.stale_updates},
+        "restarts": info.restarts, "relres": relres,
+        "step_ms_all": times, "variants": var_out, "e2e": e2e,
+        "gpu_launches": launches_per_solve * args.steps,
+        "roofline": roof, "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+
+        cores = os.cpu_count() or 1
+        spi, k = oracle_sample(A, b, oracle.partition_regular2d(N_GRID, N_GRID, PX, PX),
+                               float(os.environ.get("RAS_CPU_SAMPLE_S", "12")), cores)
+        iters = oracle_iterations()
+        line["cpu_baseline"] = {"value": spi * iters * 1e3, "unit": "ms", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{k} sync FP64 RAS iterations (local CG-20) of the "
+                                          f"same workload, extrapolated to the oracle's {iters} "
+                                          f"iterations to 1e-8"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    """Small case for ncu: the headline workload and variant, each launch
+    limited to `--profile-updates` local updates per subdomain (a few ms)."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    A, b = problem()
+    part = ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX)
+    ctx = ras.ras_setup(A, part, PX * PX, GAMMA, ras.RAS_LOCAL_CG, ras.RAS_FP32, M_INNER)
+    bd = torch.tensor(b, device="cuda")
+    tot = 0
+    for _ in range(2):
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        info = ras.ras_solve(ctx, bd, x, TOL, ras.RAS_ASYNC, args.profile_updates)
+        tot = int(ras.ras_get_update_counts(ctx).sum())
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "async_fp32", "updates_per_launch": tot,
+                      "kernel_ms": info.kernel_ms, "status": info.status}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline only (no variants, no e2e)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
+    ap.add_argument("--profile", action="store_true", help="run the small ncu case only")
+    ap.add_argument("--profile-updates", type=int, default=20)
+    args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

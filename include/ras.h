@@ -89,6 +89,8 @@ typedef struct {
   double solve_ms;        /* device time of the solve (CUDA events) */
   int32_t restarts;       /* async: post-termination checks that failed */
   int32_t status;         /* same as the return value of the solve */
+  double kernel_ms;       /* device time of the persistent RAS kernel alone */
+  int64_t stale_updates;  /* async: local solves that saw no new neighbour data */
 } ras_solve_info;
 
 /* ------------------------------------------------------------------------ */

@@ -125,7 +125,7 @@ struct DevBuf {
 };
 
 struct LaunchPlan {
-  int nt = 0, grid = 0;
+  int nt = 0, grid = 0, kmax = 0;
   size_t smem = 0;
   int Wmax = 0, npad_max = 0;
   std::vector<Item> items;
@@ -148,6 +148,7 @@ struct ras_ctx {
   int n = 0, P = 0, K = 0, overlap = 0;
   ras_local_solver ls{};
   int maxw = 0;  // largest true local half-bandwidth
+  int exec_kind = 0;  // kernel variant (LocalKind; kCGS for staged FP32 CG)
   // host copies of the maps (inspection)
   std::vector<std::vector<int32_t>> omega, iface;
   std::vector<std::vector<uint8_t>> owned;
@@ -158,6 +159,7 @@ struct ras_ctx {
   SubDesc *d_subs = nullptr;
   SubState *d_sub = nullptr;
   SysState *d_st = nullptr;
+  int16_t *d_lcol16 = nullptr;
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
   uint8_t *d_ownf = nullptr;
@@ -173,7 +175,7 @@ struct ras_ctx {
   SysState *h_st = nullptr;
   SubState *h_sub = nullptr;
   double *d_bx = nullptr;  // device b and x for ras_solve_host
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   std::vector<int64_t> last_updates;
 
   template <typename T>
@@ -214,6 +216,8 @@ struct ras_ctx {
     cudaFreeHost(h_sub);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    if (evk0) cudaEventDestroy(evk0);
+    if (evk1) cudaEventDestroy(evk1);
   }
 };
 
@@ -433,7 +437,7 @@ void assign_items(LaunchPlan &pl, const std::vector<Item> &items, const std::vec
 }
 
 ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Item> &items,
-                       const std::vector<double> &cost, int Wmax, int npad_max,
+                       const std::vector<double> &cost, int Wmax, int npad_max, int kmax,
                        cudaStream_t stream) {
   pl.release();
   int dev = 0, nsm = 0, max_smem = 0;
@@ -444,7 +448,8 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   pl.nt = main_threads(kind, nt_pref);
   pl.Wmax = Wmax;
   pl.npad_max = npad_max;
-  pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max);
+  pl.kmax = kmax;
+  pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax);
   if (pl.smem + 4096 > (size_t)max_smem) return RAS_ENOTSUP;
   const int occ = main_occupancy(kind, prec, pl.nt, pl.smem);
   if (occ <= 0) return RAS_ENOTSUP;
@@ -486,6 +491,7 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.own_l = c->d_own;
   s.fac = c->d_fac;
   s.lcol = c->d_lcol;
+  s.lcol16 = c->d_lcol16;
   s.lval = c->d_lval;
   s.luval = c->d_lu;
   s.lev_ptr = c->d_levp;
@@ -681,7 +687,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     nbrs += d.n_nbr;
     if (kind == RAS_LOCAL_BANDCHOL) {
       if (mp.w > 160) return RAS_ENOTSUP;
-      fac += 2ll * (d.npad / 32) * (d.W + 1) * 32;
+      fac += 2ll * (d.npad / 32) * 32 * slab_stride(d.W, (int)prec_bytes(prec));
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
@@ -692,6 +698,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   }
   c->plan.Wmax = kind == RAS_LOCAL_BANDCHOL ? Wmax : 0;
   c->plan.npad_max = npad_max;
+  c->exec_kind = kind;
+  if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && K <= kMaxEll && npad_max <= kStagedRows &&
+      env_int("RAS_CG_STAGE", 1) != 0)
+    c->exec_kind = kCGS;
 
   // ---- per-row host arrays
   std::vector<int32_t> gidx(rows, 0), rcol(rows * K, 0), own(owns), nbr(nbrs);
@@ -810,6 +820,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   // ---- device upload
   CUDA_TRY(cudaEventCreate(&c->ev0));
   CUDA_TRY(cudaEventCreate(&c->ev1));
+  CUDA_TRY(cudaEventCreate(&c->evk0));
+  CUDA_TRY(cudaEventCreate(&c->evk1));
   if ((st = c->upload(c->d_subs, c->subs)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_sub, P)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_st, 1)) != RAS_OK) return st;
@@ -888,6 +900,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   } else {
     std::vector<int32_t> &lc = lcol;
     if ((st = c->upload(c->d_lcol, lc)) != RAS_OK) return st;
+    if (c->exec_kind == kCGS) {
+      std::vector<int16_t> l16(lc.begin(), lc.end());
+      if ((st = c->upload(c->d_lcol16, l16)) != RAS_OK) return st;
+    }
     auto up_prec = [&](void *&dst, const std::vector<double> &src) -> ras_status {
       const size_t bytes = std::max<size_t>(src.size(), 1) * prec_bytes(prec);
       std::vector<unsigned char> tmp(bytes);
@@ -909,7 +925,11 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   // ---- default launch plan: one system, all subdomains
   std::vector<Item> items(P);
   for (int p = 0; p < P; ++p) items[p] = {0, p, 0, 0};
-  st = plan_launch(c->plan, kind, prec, items, c->cost, c->plan.Wmax, npad_max, c->stream);
+  st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax, npad_max, K, c->stream);
+  if (st == RAS_ENOTSUP && c->exec_kind == kCGS) {  // staged variant does not fit: plain CG
+    c->exec_kind = kind;
+    st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax, npad_max, K, c->stream);
+  }
   if (st != RAS_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->last_updates.assign(P, 0);
@@ -922,7 +942,8 @@ namespace {
 // Runs one full solve of the systems described by `sysdesc` with plan `pl`.
 ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &pl,
                      SysDesc *d_sys, int nsys, GridCtl *d_ctl, GridCtl *h_ctl, int32_t mode,
-                     int64_t max_updates, int m, cudaEvent_t ev0, cudaEvent_t ev1) {
+                     int64_t max_updates, int m, cudaEvent_t ev0, cudaEvent_t ev1,
+                     cudaEvent_t evk0, cudaEvent_t evk1) {
   Launch L{};
   L.sys = d_sys;
   L.nsys = nsys;
@@ -941,13 +962,16 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.Wmax = pl.Wmax;
   L.npad_max = pl.npad_max;
   L.persist = 1;
+  L.kmax = pl.kmax;
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   const int nitems = (int)pl.items.size();
   CUDA_TRY(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaEventRecord(ev0, stream));
   CUDA_TRY(launch_init(L, nitems, stream));
+  CUDA_TRY(cudaEventRecord(evk0, stream));
   CUDA_TRY(launch_main(kind, prec, pl.nt, L, pl.grid, pl.smem, stream));
+  CUDA_TRY(cudaEventRecord(evk1, stream));
   if (mode == RAS_SYNC) CUDA_TRY(launch_copyback(L, nitems, stream));
   CUDA_TRY(cudaEventRecord(ev1, stream));
   CUDA_TRY(launch_residual(L, nitems, stream));
@@ -955,12 +979,16 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
 }
 
 ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const SubState *sub,
-                       int32_t mode, ras_solve_info *info, float ms) {
+                       int32_t mode, ras_solve_info *info, float ms, float kms) {
   ras_status rs = RAS_OK;
   if (ctl.status != 0) rs = (ras_status)ctl.status;
   else if (st.status != 0) rs = (ras_status)st.status;
   std::vector<int64_t> u(c->P);
-  for (int p = 0; p < c->P; ++p) u[p] = sub[p].updates;
+  int64_t stale = 0;
+  for (int p = 0; p < c->P; ++p) {
+    u[p] = sub[p].updates;
+    stale += sub[p].stale;
+  }
   c->last_updates = u;
   if (info) {
     std::vector<int64_t> s(u);
@@ -973,6 +1001,8 @@ ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const
     info->solve_ms = ms;
     info->restarts = st.restarts;
     info->status = rs;
+    info->kernel_ms = kms;
+    info->stale_updates = stale;
   }
   return rs;
 }
@@ -986,17 +1016,19 @@ ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t
   *c->h_sysdesc = make_sysdesc(c, b, x, tol);
   CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
                            c->stream));
-  ras_status rs = run_solve(c->stream, c->ls.kind, c->ls.prec, c->plan, c->d_sysdesc, 1, c->d_ctl,
-                            c->h_ctl, mode, max_updates, c->ls.inner_iters, c->ev0, c->ev1);
+  ras_status rs = run_solve(c->stream, c->exec_kind, c->ls.prec, c->plan, c->d_sysdesc, 1, c->d_ctl,
+                            c->h_ctl, mode, max_updates, c->ls.inner_iters, c->ev0, c->ev1,
+                            c->evk0, c->evk1);
   if (rs != RAS_OK) return rs;
   CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaMemcpyAsync(c->h_sub, c->d_sub, sizeof(SubState) * c->P, cudaMemcpyDeviceToHost,
                            c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
-  float ms = 0.f;
+  float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-  return finish_info(c, *c->h_st, *c->h_ctl, c->h_sub, mode, info, ms);
+  cudaEventElapsedTime(&kms, c->evk0, c->evk1);
+  return finish_info(c, *c->h_st, *c->h_ctl, c->h_sub, mode, info, ms, kms);
 }
 
 ras_status ras_solve_host(ras_ctx *c, const double *b_host, double *x_host, double tol,
@@ -1022,7 +1054,7 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
   if (!ctxs || num <= 0 || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC))
     return RAS_EINVAL;
   for (int s = 0; s < num; ++s)
-    if (!ctxs[s] || !b[s] || !x[s] || ctxs[s]->ls.kind != ctxs[0]->ls.kind ||
+    if (!ctxs[s] || !b[s] || !x[s] || ctxs[s]->exec_kind != ctxs[0]->exec_kind ||
         ctxs[s]->ls.prec != ctxs[0]->ls.prec || ctxs[s]->ls.inner_iters != ctxs[0]->ls.inner_iters)
       return RAS_EINVAL;
   ras_ctx *c0 = ctxs[0];
@@ -1030,9 +1062,10 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
   std::vector<Item> items;
   std::vector<double> cost;
   std::vector<SysDesc> sd(num);
-  int Wmax = 0, npad_max = 0;
+  int Wmax = 0, npad_max = 0, kmax = 0;
   for (int s = 0; s < num; ++s) {
     ras_ctx *c = ctxs[s];
+    kmax = std::max(kmax, c->K);
     // one solve at a time per context: the state buffers are per context
     for (int t = 0; t < s; ++t)
       if (ctxs[t] == c) return RAS_EINVAL;
@@ -1045,7 +1078,7 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
     npad_max = std::max(npad_max, c->plan.npad_max);
   }
   LaunchPlan pl;
-  ras_status rs = plan_launch(pl, c0->ls.kind, c0->ls.prec, items, cost, Wmax, npad_max, stream);
+  ras_status rs = plan_launch(pl, c0->exec_kind, c0->ls.prec, items, cost, Wmax, npad_max, kmax, stream);
   if (rs != RAS_OK) {
     pl.release();
     return rs;
@@ -1066,8 +1099,8 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
     return RAS_ENOMEM;
   }
   cudaMemcpyAsync(d_sys, sd.data(), sizeof(SysDesc) * num, cudaMemcpyHostToDevice, stream);
-  rs = run_solve(stream, c0->ls.kind, c0->ls.prec, pl, d_sys, num, d_ctl, &h_ctl, mode,
-                 max_updates, c0->ls.inner_iters, c0->ev0, c0->ev1);
+  rs = run_solve(stream, c0->exec_kind, c0->ls.prec, pl, d_sys, num, d_ctl, &h_ctl, mode,
+                 max_updates, c0->ls.inner_iters, c0->ev0, c0->ev1, c0->evk0, c0->evk1);
   if (rs != RAS_OK) {
     cleanup();
     return rs;
@@ -1081,14 +1114,15 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
                     cudaMemcpyDeviceToHost, stream);
   }
   cudaError_t e = cudaStreamSynchronize(stream);
-  float ms = 0.f;
+  float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, c0->ev0, c0->ev1);
+  cudaEventElapsedTime(&kms, c0->evk0, c0->evk1);
   cleanup();
   if (e != cudaSuccess) return RAS_ECUDA;
   ras_status first = RAS_OK;
   for (int s = 0; s < num; ++s) {
     ras_status r = finish_info(ctxs[s], hst[s], h_ctl, hsub[s].data(), mode,
-                               infos ? &infos[s] : nullptr, ms);
+                               infos ? &infos[s] : nullptr, ms, kms);
     if (first == RAS_OK && r != RAS_OK) first = r;
   }
   return first;

@@ -18,7 +18,8 @@
 
 namespace ras {
 
-enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2 };
+enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2,
+                          kCGS = 3 };  // kCGS: CG with A_p staged in shared memory (kernel variant)
 enum Prec : int32_t { kF64 = 0, kF32 = 1, kBF16 = 2 };
 enum Mode : int32_t { kSync = 0, kAsync = 1 };
 // status codes (mirror ras_status)
@@ -90,6 +91,7 @@ struct SysDesc {
   const int32_t *own_l;
   const void *fac;
   const int32_t *lcol;
+  const int16_t *lcol16;  // local columns as int16 (staged CG)
   const void *lval;
   const void *luval;
   const int32_t *lev_ptr;
@@ -105,6 +107,8 @@ struct Item {
 };
 
 constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
+constexpr int kMaxEll = 8;      // ELL widths up to this are fully unrolled
+constexpr int kStagedRows = 6144;  // largest subdomain of the staged CG variant
 
 struct GridCtl {
   unsigned int count;  // barrier arrivals
@@ -134,7 +138,7 @@ struct Launch {
   int32_t Wmax;                // band: max W over the launch
   int32_t npad_max;
   int32_t persist;             // async: keep polling until every system is done
-  int32_t pad_;
+  int32_t kmax;                // largest ELL width over the launch
 };
 
 }  // namespace ras

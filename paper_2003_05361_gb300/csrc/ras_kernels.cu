@@ -203,6 +203,14 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void bulk_copy_nobar_arrive(void *dst, const void *src, uint32_t bytes,
+                                                       uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -301,16 +309,19 @@ __global__ void __launch_bounds__(256) band_chol_kernel(const BandJob *jobs, dou
 // --------------------------------------------------------------------------
 //
 // Rows are grouped in blocks of 32. With W = storage half-width (>= 31 and
-// >= the true half-width w), block K's FORWARD slab F[t][l] (t = 0..W,
-// l = 0..31, row i = 32K + l) holds
+// >= the true half-width w) and S = slab_stride(W), block K's FORWARD slab
+// holds for each lane l (row i = 32K + l) a contiguous row F[l][0..S):
 //   t <  W - l : L[i][i - W + t]            (columns left of the block)
-//   t >= W - l : Linv_KK[l][l - (W - t)]    (inverse of the diagonal block)
-// and its BACKWARD slab Bk[d][l] holds, for U = L^T,
+//   W-l <= t <= W : Linv_KK[l][t - (W - l)]  (row l of the inverse diagonal block)
+//   t >  W : 0
+// and its BACKWARD slab, for U = L^T, B[l][0..S):
 //   d <  32 - l : Uinv_KK[l][l + d] = Linv_KK[l + d][l]
-//   d >= 32 - l : U[i][i + d] = L[i + d][i] (columns right of the block)
+//   32-l <= d <= W : U[i][i + d] = L[i + d][i]   (columns right of the block)
+//   d >  W : 0
 // so the forward step of block K is  y_K = Linv_KK (r_K - L_{K,left} y_left)
-// and the backward step  z_K = Uinv_KK (y_K - U_{K,right} z_right), each row
-// reading exactly w+1 useful entries. Rows i >= n are identity rows.
+// and the backward step  z_K = Uinv_KK (y_K - U_{K,right} z_right); each row
+// reads its w+1 useful entries from one contiguous slab. Rows i >= n are
+// identity rows.
 template <typename T>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
@@ -319,6 +330,7 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
   const LayoutJob jb = jobs[blockIdx.x];
   const int l = threadIdx.x;
   const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, ld = w + 1;
+  const int S = slab_stride(W, (int)sizeof(T));
   const double *Bd = band + jb.band_off;
   const int i = 32 * K + l;
   // diagonal block, row l
@@ -351,29 +363,29 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) X[r][m] = col[r];
   }
   __syncwarp();
-  const int64_t slab = (int64_t)(W + 1) * 32;
-  T *F = fac + jb.fac_off + (int64_t)K * slab;
-  T *Bk = fac + jb.fac_off + (int64_t)jb.nb * slab + (int64_t)K * slab;
-  for (int t = 0; t <= W; ++t) {
-    double v;
+  const int64_t slab = (int64_t)32 * S;
+  T *F = fac + jb.fac_off + (int64_t)K * slab + (int64_t)l * S;
+  T *Bk = fac + jb.fac_off + (int64_t)jb.nb * slab + (int64_t)K * slab + (int64_t)l * S;
+  for (int t = 0; t < S; ++t) {
+    double v = 0.0;
     if (t < W - l) {
       const int jcol = i - W + t;
       const int tb = t - W + w;  // index in the stored band row
       v = (i < n && jcol >= 0 && tb >= 0) ? Bd[(int64_t)i * ld + tb] : 0.0;
-    } else {
-      v = X[l][l - (W - t)];
+    } else if (t <= W) {
+      v = X[l][t - (W - l)];
     }
-    F[(int64_t)t * 32 + l] = from_double<T>(v);
+    F[t] = from_double<T>(v);
   }
-  for (int d = 0; d <= W; ++d) {
-    double v;
+  for (int d = 0; d < S; ++d) {
+    double v = 0.0;
     if (d < 32 - l) {
       v = X[l + d][l];
-    } else {
+    } else if (d <= W) {
       const int r = i + d;
       v = (i < n && r < n && d <= w) ? Bd[(int64_t)r * ld + (w - d)] : 0.0;
     }
-    Bk[(int64_t)d * 32 + l] = from_double<T>(v);
+    Bk[d] = from_double<T>(v);
   }
 }
 
@@ -478,18 +490,158 @@ __global__ void __launch_bounds__(128) ras_copyback_kernel(Launch L) {
 // local solvers
 // --------------------------------------------------------------------------
 
+// 16-byte vector loads from shared memory, widened to the compute type.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  static constexpr int V = 4;
+  __device__ __forceinline__ static void load(const float *p, float *o) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct Vec16<double> {
+  static constexpr int V = 2;
+  __device__ __forceinline__ static void load(const double *p, double *o) {
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+template <> struct Vec16<__nv_bfloat16> {
+  static constexpr int V = 8;
+  __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float *o) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 h;
+      memcpy(&h, &w[j], 4);
+      const float2 f = __bfloat1622float2(h);
+      o[2 * j] = f.x;
+      o[2 * j + 1] = f.y;
+    }
+  }
+};
+
+// One forward block (lane l, row i = 32K + l): c = r_i - sum_{t < W-l} F[l][t] y[i-W+t],
+// then y_i = sum_{m <= l} Linv[l][m] c_m. `row` is this lane's slab row, y is
+// indexed so that y[0] is global row 0.
+template <typename T, typename CT>
+__device__ __forceinline__ void band_fwd_block(const T *row, CT *y, int i, int W, int lane,
+                                               CT *cbuf) {
+  using VL = Vec16<T>;
+  constexpr int V = VL::V;
+  const CT *yb = y + i - W;
+  CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
+  const int tfull = ((W - 31) / V) * V;  // t < tfull: every lane is off-block
+  for (int t = 0; t < tfull; t += V) {
+    CT v[V];
+    VL::load(row + t, v);
+#pragma unroll
+    for (int u = 0; u < V; u += 4) {
+      a0 -= v[u] * yb[t + u];
+      if (u + 1 < V) a1 -= v[u + 1] * yb[t + u + 1];
+      if (u + 2 < V) a2 -= v[u + 2] * yb[t + u + 2];
+      if (u + 3 < V) a3 -= v[u + 3] * yb[t + u + 3];
+    }
+  }
+  const int lim = W - lane;
+  for (int t = tfull; t < W; t += V) {
+    CT v[V];
+    VL::load(row + t, v);
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+      if (t + u < lim) {
+        const CT pr = v[u] * yb[t + u];
+        if ((u & 3) == 0) a0 -= pr;
+        else if ((u & 3) == 1) a1 -= pr;
+        else if ((u & 3) == 2) a2 -= pr;
+        else a3 -= pr;
+      }
+  }
+  cbuf[lane] = (a0 + a1) + (a2 + a3);
+  __syncwarp();
+  const T *rb = row + W - lane;  // rb[m] = Linv[lane][m]
+  CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
+#pragma unroll
+  for (int m = 0; m < 32; m += 4) {
+    if (m <= lane) b0 += to_ct(rb[m]) * cbuf[m];
+    if (m + 1 <= lane) b1 += to_ct(rb[m + 1]) * cbuf[m + 1];
+    if (m + 2 <= lane) b2 += to_ct(rb[m + 2]) * cbuf[m + 2];
+    if (m + 3 <= lane) b3 += to_ct(rb[m + 3]) * cbuf[m + 3];
+  }
+  y[i] = (b0 + b1) + (b2 + b3);
+  __syncwarp();
+}
+
+// One backward block: c = y_i - sum_{32-l <= d <= W} B[l][d] z[i+d], then
+// z_i = sum_{d <= 31-l} Uinv[l][l+d] c_{l+d}.
+template <typename T, typename CT>
+__device__ __forceinline__ void band_bwd_block(const T *row, CT *y, int i, int W, int lane,
+                                               CT *cbuf) {
+  using VL = Vec16<T>;
+  constexpr int V = VL::V;
+  const CT *zb = y + i;
+  CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
+  const int d0 = 32 - lane;
+  for (int d = 0; d < 32; d += V) {
+    CT v[V];
+    VL::load(row + d, v);
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+      if (d + u >= d0 && d + u <= W) {
+        const CT pr = v[u] * zb[d + u];
+        if ((u & 3) == 0) a0 -= pr;
+        else if ((u & 3) == 1) a1 -= pr;
+        else if ((u & 3) == 2) a2 -= pr;
+        else a3 -= pr;
+      }
+  }
+  // d in [32, S): slab entries beyond W are zero, z beyond the subdomain is zero
+  for (int d = 32; d <= W; d += V) {
+    CT v[V];
+    VL::load(row + d, v);
+#pragma unroll
+    for (int u = 0; u < V; u += 4) {
+      a0 -= v[u] * zb[d + u];
+      if (u + 1 < V) a1 -= v[u + 1] * zb[d + u + 1];
+      if (u + 2 < V) a2 -= v[u + 2] * zb[d + u + 2];
+      if (u + 3 < V) a3 -= v[u + 3] * zb[d + u + 3];
+    }
+  }
+  cbuf[lane] = (a0 + a1) + (a2 + a3);
+  __syncwarp();
+  CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
+#pragma unroll
+  for (int d = 0; d < 32; d += V) {
+    CT v[V];
+    VL::load(row + d, v);
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+      if (d + u < 32 - lane) {
+        const CT pr = v[u] * cbuf[lane + d + u];
+        if ((u & 3) == 0) b0 += pr;
+        else if ((u & 3) == 1) b1 += pr;
+        else if ((u & 3) == 2) b2 += pr;
+        else b3 += pr;
+      }
+  }
+  y[i] = (b0 + b1) + (b2 + b3);
+  __syncwarp();
+}
+
 // Banded Cholesky solve L L^T delta = r by warp 0. y[OFF + i] holds r on entry
-// and delta on exit; y[0, OFF) and y[OFF+npad, OFF+npad+W] must be zero.
+// and delta on exit; y[0, OFF) and y[OFF+npad, OFF+npad+W+16) must be zero.
 // Slabs stream through an NS-stage ring of shared memory with bulk copies
-// (cp.async.bulk + mbarrier), NS-1 blocks ahead of the block being solved.
+// (cp.async.bulk + mbarrier), up to NS blocks ahead of the block being solved.
 // gcount: running slab count of this CTA (selects stage and parity).
 template <typename T, typename CT, int NS>
 __device__ bool band_solve_warp(const T *slabF, const T *slabB, int nb, int W, CT *y, int OFF,
                                 CT *cbuf, T *ring, int ring_stride, uint64_t *mbar,
                                 uint32_t &gcount, int64_t timeout_ns) {
   const int lane = threadIdx.x & 31;
-  const uint32_t bytes = (uint32_t)((W + 1) * 32 * sizeof(T));
-  const int64_t slab = (int64_t)(W + 1) * 32;
+  const int S = slab_stride(W, (int)sizeof(T));
+  const int64_t slab = (int64_t)32 * S;
+  const uint32_t bytes = (uint32_t)(slab * sizeof(T));
   bool ok = true;
   for (int dir = 0; dir < 2; ++dir) {
     const T *base = dir == 0 ? slabF : slabB;
@@ -510,53 +662,10 @@ __device__ bool band_solve_warp(const T *slabF, const T *slabB, int nb, int W, C
       const uint32_t st = g % NS;
       const uint32_t par = (g / NS) & 1u;
       if (!mbar_wait(&mbar[st], par, timeout_ns)) { ok = false; break; }
-      const T *sl = ring + st * ring_stride;
+      const T *row = ring + st * ring_stride + lane * S;
       const int K = dir == 0 ? s : nb - 1 - s;
-      const int i = 32 * K + lane;
-      if (dir == 0) {
-        // c = r_K - L_{K,left} y_left
-        CT a0 = y[OFF + i], a1 = CT(0);
-        const CT *yb = y + OFF + i - W;
-        const int lim = W - lane;
-        int t = 0;
-        for (; t + 1 < lim; t += 2) {
-          a0 -= to_ct(sl[t * 32 + lane]) * yb[t];
-          a1 -= to_ct(sl[(t + 1) * 32 + lane]) * yb[t + 1];
-        }
-        if (t < lim) a0 -= to_ct(sl[t * 32 + lane]) * yb[t];
-        cbuf[lane] = a0 + a1;
-        __syncwarp();
-        CT v0 = CT(0), v1 = CT(0);
-        int e = 0;
-        for (; e + 1 <= lane; e += 2) {
-          v0 += to_ct(sl[(W - e) * 32 + lane]) * cbuf[lane - e];
-          v1 += to_ct(sl[(W - e - 1) * 32 + lane]) * cbuf[lane - e - 1];
-        }
-        if (e <= lane) v0 += to_ct(sl[(W - e) * 32 + lane]) * cbuf[lane - e];
-        y[OFF + i] = v0 + v1;
-      } else {
-        // c = y_K - U_{K,right} z_right
-        CT a0 = y[OFF + i], a1 = CT(0);
-        int d = 32 - lane;
-        for (; d + 1 <= W; d += 2) {
-          a0 -= to_ct(sl[d * 32 + lane]) * y[OFF + i + d];
-          a1 -= to_ct(sl[(d + 1) * 32 + lane]) * y[OFF + i + d + 1];
-        }
-        if (d <= W) a0 -= to_ct(sl[d * 32 + lane]) * y[OFF + i + d];
-        cbuf[lane] = a0 + a1;
-        __syncwarp();
-        CT v0 = CT(0), v1 = CT(0);
-        const int lim = 32 - lane;
-        int e = 0;
-        for (; e + 1 < lim; e += 2) {
-          v0 += to_ct(sl[e * 32 + lane]) * cbuf[lane + e];
-          v1 += to_ct(sl[(e + 1) * 32 + lane]) * cbuf[lane + e + 1];
-        }
-        if (e < lim) v0 += to_ct(sl[e * 32 + lane]) * cbuf[lane + e];
-        __syncwarp();
-        y[OFF + i] = v0 + v1;
-      }
-      __syncwarp();
+      if (dir == 0) band_fwd_block<T, CT>(row, y + OFF, 32 * K + lane, W, lane, cbuf);
+      else band_bwd_block<T, CT>(row, y + OFF, 32 * K + lane, W, lane, cbuf);
       // refill the stage just consumed
       if (issued < nb) {
         if (lane == 0) {
@@ -619,6 +728,70 @@ __device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad,
     for (int i = threadIdx.x; i < n; i += NT) p[i] = r[i] + beta * p[i];
     __syncthreads();
   }
+}
+
+// m steps of textbook CG with A_p staged in shared memory (FP32 values,
+// int16 local columns) and the vectors r, d, q in registers: thread t owns
+// rows t, t + NT, t + 2 NT, ... Only p lives in shared memory. On entry p
+// holds r (zero beyond n); on exit it holds d.
+template <int NT, int RMAX>
+__device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
+                                int m, float *p, float *red) {
+  const int tid = threadIdx.x;
+  float r[RMAX], d[RMAX], q[RMAX];
+  float rr = 0.f;
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    const int i = tid + k * NT;
+    r[k] = i < n ? p[i] : 0.f;
+    d[k] = 0.f;
+    q[k] = 0.f;
+    rr += r[k] * r[k];
+  }
+  rr = block_sum<NT, float>(rr, red);
+  for (int it = 0; it < m && rr != 0.f; ++it) {
+    float pq = 0.f;
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+      const int i = tid + k * NT;
+      if (i < n) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < kMaxEll; ++e)
+          if (e < K) s += sval[e * npad + i] * p[scol[e * npad + i]];
+        q[k] = s;
+        pq += p[i] * s;
+      }
+    }
+    pq = block_sum<NT, float>(pq, red);
+    const float alpha = rr / pq;
+    float rn = 0.f;
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+      const int i = tid + k * NT;
+      if (i < n) {
+        d[k] += alpha * p[i];
+        r[k] -= alpha * q[k];
+        rn += r[k] * r[k];
+      }
+    }
+    rn = block_sum<NT, float>(rn, red);
+    const float beta = rn / rr;
+    rr = rn;
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+      const int i = tid + k * NT;
+      if (i < n) p[i] = r[k] + beta * p[i];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    const int i = tid + k * NT;
+    if (i < npad) p[i] = i < n ? d[k] : 0.f;
+  }
+  __syncthreads();
 }
 
 // z = U^{-1} L^{-1} r with the ILU(0) factors, level by level.
@@ -712,23 +885,32 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
 // the persistent RAS kernel
 // --------------------------------------------------------------------------
 
-constexpr int kBandStages = 3;
+constexpr int kBandStages = 4;
+constexpr int kYPad = 48;  // zero tail of y beyond W (vector overrun of the last chunk)
 
 template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
   // band: ring | y | cbuf ; cg: r p q d ; ilu: r z p q d
   static __host__ __device__ size_t ring_stride(int Wmax) {
-    const size_t b = (size_t)(Wmax + 1) * 32 * sizeof(T);
+    const size_t b = (size_t)slab_stride(Wmax, (int)sizeof(T)) * 32 * sizeof(T);
     return ((b + 127) / 128) * 128 / sizeof(T);
   }
+  static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
+    return ((size_t)(2 * Wmax + npad_max + kYPad) + 31) / 32 * 32;
+  }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
-  static __host__ __device__ size_t bytes(int Wmax, int npad_max) {
+  static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax) {
     if (KIND == kBand) {
       size_t b = kBandStages * ring_stride(Wmax) * sizeof(T);
-      b += ((size_t)(2 * Wmax + npad_max + 1 + 31) / 32 * 32) * sizeof(CT);
-      b += 32 * sizeof(CT);
+      b += ylen(Wmax, npad_max) * sizeof(CT);
+      b += 64 * sizeof(CT);
       return b;
+    }
+    if (KIND == kCGS) {
+      // values (FP32) | columns (int16) | p ; K <= kmax <= kMaxEll
+      const size_t vl = vec_len(npad_max);
+      return (size_t)kmax * vl * 6 + vl * 4;
     }
     const int nv = KIND == kCG ? 4 : 5;
     return nv * vec_len(npad_max) * sizeof(CT);
@@ -765,7 +947,10 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     ring_stride = (int)SM::ring_stride(L.Wmax);
     ring = reinterpret_cast<T *>(smem);
     ybuf = reinterpret_cast<CT *>(smem + kBandStages * ring_stride * sizeof(T));
-    cbuf = ybuf + (2 * L.Wmax + L.npad_max + 1 + 31) / 32 * 32;
+    cbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
+  } else if (KIND == kCGS) {
+    const size_t vl = SM::vec_len(L.npad_max);
+    v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
   } else {
     const size_t vl = SM::vec_len(L.npad_max);
     CT *base = reinterpret_cast<CT *>(smem);
@@ -776,7 +961,7 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     v4 = KIND == kILU ? base + 4 * vl : nullptr;
   }
   uint32_t gcount = 0;
-  if (KIND == kBand) {
+  if (KIND == kBand || KIND == kCGS) {
     if (tid == 0) {
       for (int s = 0; s < kBandStages; ++s) mbar_init(&s_mbar[s], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -804,17 +989,44 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     const int K = S.K;
     const int64_t eb = D.row_off * K;
     CT *rhs = KIND == kBand ? ybuf + OFF : v0;
+    if (KIND == kCGS && tid == 0) {
+      // stage A_p (values, columns) while the residual is gathered
+      const size_t vl = SM::vec_len(L.npad_max);
+      const uint32_t bv = (uint32_t)((size_t)K * D.npad * 4), bc = (uint32_t)((size_t)K * D.npad * 2);
+      fence_proxy_async();
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_mbar[0])),
+                   "r"(bv + bc)
+                   : "memory");
+      bulk_copy_nobar_arrive(smem, reinterpret_cast<const float *>(S.lval) + D.row_off * K, bv, &s_mbar[0]);
+      bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.lcol16 + D.row_off * K, bc, &s_mbar[0]);
+    }
     if (KIND == kBand) {
       // zero the halo of y (head and tail)
       for (int e = tid; e < OFF; e += NT) ybuf[e] = CT(0);
-      for (int e = tid; e <= L.Wmax; e += NT) ybuf[OFF + D.npad + e] = CT(0);
+      for (int e = tid; e < L.Wmax + kYPad; e += NT) ybuf[OFF + D.npad + e] = CT(0);
     }
     double a_loc = 0.0, a_own = 0.0;
     for (int i = tid; i < D.npad; i += NT) {
       double r = 0.0;
       if (i < D.n) {
         r = S.b[S.gidx[D.row_off + i]];
-        for (int k = 0; k < K; ++k) {
+        // issue every column / value / x load of the row before the arithmetic
+        int cols[kMaxEll];
+        double vals[kMaxEll], xs[kMaxEll];
+#pragma unroll
+        for (int k = 0; k < kMaxEll; ++k)
+          if (k < K) {
+            const int64_t e = eb + (int64_t)k * D.npad + i;
+            cols[k] = S.rcol[e];
+            vals[k] = S.rval[e];
+          }
+#pragma unroll
+        for (int k = 0; k < kMaxEll; ++k)
+          if (k < K) xs[k] = async ? ld_relaxed_f64(xcur + cols[k]) : __ldcg(xcur + cols[k]);
+#pragma unroll
+        for (int k = 0; k < kMaxEll; ++k)
+          if (k < K) r -= vals[k] * xs[k];
+        for (int k = kMaxEll; k < K; ++k) {
           const int64_t e = eb + (int64_t)k * D.npad + i;
           const double xv = async ? ld_relaxed_f64(xcur + S.rcol[e]) : __ldcg(xcur + S.rcol[e]);
           r -= S.rval[e] * xv;
@@ -833,7 +1045,7 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
       bool ok = true;
       if (tid < 32) {
         const T *fac = reinterpret_cast<const T *>(S.fac);
-        const int64_t slab = (int64_t)(D.W + 1) * 32;
+        const int64_t slab = (int64_t)32 * slab_stride(D.W, (int)sizeof(T));
         const int nb = D.npad / 32;
         ok = band_solve_warp<T, CT, kBandStages>(fac + D.fac_off, fac + D.fac_off + nb * slab, nb,
                                                  D.W, ybuf, OFF, cbuf, ring, ring_stride, s_mbar,
@@ -843,6 +1055,23 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
       }
       __syncthreads();
       if (!s_flag[4]) return false;
+    } else if (KIND == kCGS) {
+      if (tid == 0) {
+        const bool ok = mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);
+        if (!ok) {
+          set_error(L.ctl, kETIMEOUT, 5);
+          mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);  // bounded drain of the copy
+        }
+        s_flag[4] = ok ? 1 : 0;
+      }
+      ++gcount;
+      __syncthreads();
+      if (!s_flag[4]) return false;
+      const size_t vl = SM::vec_len(L.npad_max);
+      cg_solve_staged<NT, (kStagedRows + NT - 1) / NT>(
+          reinterpret_cast<const float *>(smem), reinterpret_cast<const int16_t *>(smem + (size_t)L.kmax * vl * 4),
+          K, D.n, D.npad, L.m, reinterpret_cast<float *>(v0), reinterpret_cast<float *>(s_redc));
+      delta = v0;
     } else if (KIND == kCG) {
       const int32_t *lc = S.lcol + D.row_off * K;
       const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
@@ -1123,9 +1352,11 @@ static int occupancy_t(size_t smem) {
 #define RAS_DISPATCH(KIND_, PREC_, NT_, CALL)                                              \
   do {                                                                                     \
     if (KIND_ == kBand) {                                                                  \
-      if (PREC_ == kF64) { CALL(kBand, double, 128); }                                     \
-      else if (PREC_ == kF32) { CALL(kBand, float, 128); }                                 \
-      else { CALL(kBand, __nv_bfloat16, 128); }                                            \
+      if (PREC_ == kF64) { CALL(kBand, double, 256); }                                     \
+      else if (PREC_ == kF32) { CALL(kBand, float, 256); }                                 \
+      else { CALL(kBand, __nv_bfloat16, 256); }                                            \
+    } else if (KIND_ == kCGS) {                                                            \
+      CALL(kCGS, float, 512);                                                              \
     } else if (KIND_ == kCG) {                                                             \
       if (PREC_ == kF64) { if (NT_ == 512) { CALL(kCG, double, 512); } else { CALL(kCG, double, 256); } } \
       else { if (NT_ == 512) { CALL(kCG, float, 512); } else { CALL(kCG, float, 256); } }  \
@@ -1135,16 +1366,17 @@ static int occupancy_t(size_t smem) {
     }                                                                                      \
   } while (0)
 
-size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max) {
+size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax) {
   size_t r = 0;
-#define RAS_SMEM(K_, T_, NT_) r = Smem<K_, T_, NT_>::bytes(Wmax, npad_max)
+#define RAS_SMEM(K_, T_, NT_) r = Smem<K_, T_, NT_>::bytes(Wmax, npad_max, kmax)
   RAS_DISPATCH(kind, prec, nt, RAS_SMEM);
 #undef RAS_SMEM
   return r;
 }
 
 int main_threads(int kind, int nt_pref) {
-  if (kind == kBand) return 128;
+  if (kind == kBand) return 256;
+  if (kind == kCGS) return 512;
   return nt_pref == 512 ? 512 : 256;
 }
 
