@@ -387,23 +387,33 @@ def run_ours(args):
 
 
 def run_profile_case(args):
-    """Small case for ncu: the headline workload and variant, each launch
-    limited to `--profile-updates` local updates per subdomain (a few ms)."""
+    """Small cases for ncu, each launch capped at `--profile-updates` local
+    updates per subdomain (a few ms):
+      cg_cfg2   the benchmark workload, async, FP32 local CG-20 (default);
+      band_cfg1 2D Poisson 128^2, 2x2, overlap 2, banded Cholesky FP32, sync."""
     import torch
 
     import paper_2003_05361_gb300 as ras
 
-    A, b = problem()
-    part = ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX)
-    ctx = ras.ras_setup(A, part, PX * PX, GAMMA, ras.RAS_LOCAL_CG, ras.RAS_FP32, M_INNER)
+    if args.case == "band_cfg1":
+        A = problems.poisson2d(128)
+        b, _, _ = problems.rhs_eigen2d(128)
+        part = ras.ras_partition_regular2d(128, 128, 2, 2)
+        ctx = ras.ras_setup(A, part, 4, 2, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP32)
+        mode, variant = ras.RAS_SYNC, "sync_band_fp32_cfg1"
+    else:
+        A, b = problem()
+        part = ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX)
+        ctx = ras.ras_setup(A, part, PX * PX, GAMMA, ras.RAS_LOCAL_CG, ras.RAS_FP32, M_INNER)
+        mode, variant = ras.RAS_ASYNC, "async_fp32"
     bd = torch.tensor(b, device="cuda")
     tot = 0
     for _ in range(2):
         x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-        info = ras.ras_solve(ctx, bd, x, TOL, ras.RAS_ASYNC, args.profile_updates)
+        info = ras.ras_solve(ctx, bd, x, TOL, mode, args.profile_updates)
         tot = int(ras.ras_get_update_counts(ctx).sum())
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "async_fp32", "updates_per_launch": tot,
+    print(json.dumps({"profile_case": variant, "updates_per_launch": tot,
                       "kernel_ms": info.kernel_ms, "status": info.status}))
 
 
@@ -417,6 +427,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--profile", action="store_true", help="run the small ncu case only")
     ap.add_argument("--profile-updates", type=int, default=20)
+    ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1"])
     args = ap.parse_args()
     if args.profile:
         run_profile_case(args)

@@ -1003,6 +1003,7 @@ ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const
     info->status = rs;
     info->kernel_ms = kms;
     info->stale_updates = stale;
+    info->error_site = ctl.status == RAS_ETIMEOUT ? (int32_t)ctl.err_info : 0;
   }
   return rs;
 }

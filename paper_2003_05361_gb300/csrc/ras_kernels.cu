@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
   }
   for (int k = tid; k < nls; k += NT) {
     const int sys = L.cta_sys[2 * (cs0 + k)];
-    s_done[k] = 0;
+    s_done[k] = L.sys[sys].st->done;  // systems finished in an earlier launch stay finished
     s_iter0[k] = L.sys[sys].st->iters;
   }
   __syncthreads();
