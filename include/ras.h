@@ -179,6 +179,26 @@ ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
  * (b, x DEVICE). Synchronises the context's stream. */
 ras_status ras_relres(ras_ctx *ctx, const double *b, const double *x, double *relres);
 
+/* No-allocation relative residual, for callers that cannot call cudaMalloc
+ * (code running during CUDA graph capture, programs whose device memory
+ * belongs to a fixed pool or custom allocator, loops that must not allocate
+ * after start-up). The paper has no counterpart: it is an operational entry
+ * point of this library. Computes ||b - A x||_2 / ||b||_2 (or ||b - A x||_2
+ * when b = 0) in FP64 for a caller-held DEVICE CSR matrix (row_ptr[n+1],
+ * col_idx, val, same rules as ras_csr) and DEVICE vectors b[n], x[n], and
+ * writes it to the DEVICE double *relres, stream-ordered on cuda_stream
+ * (NULL = legacy default stream); it does not synchronise. It allocates
+ * nothing: its scratch (one pair of partial sums per 1024 rows) is a
+ * 1 MiB file-scope device array that every GPU loading the library holds
+ * until exit, so n may be at most 67,108,864 (larger n: RAS_EINVAL). The
+ * first call on a device looks the array's address up with that device
+ * current; make that first call before any stream capture. All calls share
+ * the array: calls that overlap on the GPU race and must be ordered by the
+ * caller. */
+ras_status ras_relres_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                              const double *val, const double *b, const double *x, double *relres,
+                              void *cuda_stream);
+
 /* Static description of a status code. */
 const char *ras_status_str(ras_status status);
 

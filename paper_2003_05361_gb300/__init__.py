@@ -84,6 +84,7 @@ def load():
                              C.c_int),
             "ras_get_update_counts": ([P, P], C.c_int),
             "ras_relres": ([P, P, P, C.POINTER(D)], C.c_int),
+            "ras_relres_noalloc": ([I32, P, P, P, P, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -256,3 +257,17 @@ def ras_relres(ctx: RasContext, b, x) -> float:
     r = C.c_double()
     _check(load().ras_relres(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x, ctx.n, "x"), C.byref(r)), "ras_relres")
     return r.value
+
+
+def ras_relres_noalloc(row_ptr, col_idx, val, b, x, out, stream=None) -> None:
+    """No-allocation relative residual (see include/ras.h): every argument is
+    a device tensor (int32 row_ptr / col_idx, float64 val / b / x, and a
+    one-element float64 `out` that receives the result, stream-ordered)."""
+    n = row_ptr.numel() - 1
+    for t, dt, what in ((row_ptr, "int32", "row_ptr"), (col_idx, "int32", "col_idx")):
+        if not (t.is_cuda and str(t.dtype).endswith(dt) and t.is_contiguous()):
+            raise TypeError(f"{what} must be a contiguous {dt} CUDA tensor")
+    _check(load().ras_relres_noalloc(n, row_ptr.data_ptr(), col_idx.data_ptr(),
+                                     _dptr(val, None, "val"), _dptr(b, n, "b"), _dptr(x, n, "x"),
+                                     _dptr(out, 1, "out"), _stream_handle(stream)),
+           "ras_relres_noalloc")

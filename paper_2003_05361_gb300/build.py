@@ -32,7 +32,7 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    srcs = [os.path.join(CSRC, f) for f in ("ras_kernels.cu", "ras_api.cpp")]
+    srcs = [os.path.join(CSRC, f) for f in ("ras_kernels.cu", "ras_api.cpp", "ras_noalloc.cu")]
     deps = srcs + [os.path.join(CSRC, f) for f in ("ras_internal.h", "ras_launch.h")]
     deps.append(os.path.join(ROOT, "include", "ras.h"))
     return srcs, deps
@@ -56,11 +56,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tag = f".{os.getpid()}"
     obj_cu = os.path.join(OUT, f"ras_kernels{tag}.o")
     obj_cpp = os.path.join(OUT, f"ras_api{tag}.o")
+    obj_na = os.path.join(OUT, f"ras_noalloc{tag}.o")
     cmds = [
         [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", srcs[0],
          "-o", obj_cu],
         ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-pthread",
          f"-I{os.path.join(cuda, 'include')}", "-c", srcs[1], "-o", obj_cpp],
+        [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", srcs[2],
+         "-o", obj_na],
     ]
 
     def run(cmd):
@@ -71,12 +74,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"build failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return r
 
-    with ThreadPoolExecutor(2) as ex:
+    with ThreadPoolExecutor(3) as ex:
         list(ex.map(run, cmds))
     tmp = os.path.join(OUT, f"libras{tag}.so")
-    run([nvcc, *ARCH, "-shared", "-o", tmp, obj_cu, obj_cpp, "-lpthread"])
+    run([nvcc, *ARCH, "-shared", "-o", tmp, obj_cu, obj_cpp, obj_na, "-lpthread"])
     os.replace(tmp, LIB)
-    for o in (obj_cu, obj_cpp):
+    for o in (obj_cu, obj_cpp, obj_na):
         os.remove(o)
     return LIB
 
