@@ -417,6 +417,35 @@ def run_profile_case(args):
                       "kernel_ms": info.kernel_ms, "status": info.status}))
 
 
+def run_serving(args):
+    """Serving workload: a seeded Poisson stream of 2D Poisson solves with sides
+    uniform in 64..512 (64 x 64 subdomains, overlap 2, banded Cholesky),
+    served by continuous batching; async mixed precision (FP32 factors) vs
+    sync FP64. Reports p50 / p99 latency (completion - arrival) and solves/s.
+    The stream length and rate are bounded so the run takes about a minute."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+    from paper_2003_05361_gb300.serve import Server, request_stream
+
+    torch.cuda.set_device(0)
+    out = {}
+    for name, mode, prec in (("async_fp32", ras.RAS_ASYNC, ras.RAS_FP32),
+                             ("sync_fp64", ras.RAS_SYNC, ras.RAS_FP64)):
+        reqs = request_stream(args.serve_requests, rate=args.serve_rate, seed=5)
+        srv = Server(mode=mode, prec=prec, step_limit=args.serve_step)
+        stats = srv.run(reqs)
+        out[name] = stats
+        print(json.dumps({"serving": name, **stats}), flush=True)
+    line = {"metric": "serving p50/p99 latency and solves/s (continuous batching)",
+            "unit": "ms", "value": out["async_fp32"].get("p99_ms"), "higher_is_better": False,
+            "config": {"workload": f"{args.serve_requests} seeded Poisson-arrival 2D Poisson solves, "
+                                   f"side U{{64..512}}, rate {args.serve_rate}/s, 64x64 subdomains, "
+                                   "overlap 2, banded Cholesky, tol 1e-8"},
+            "variants": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -428,8 +457,14 @@ def main():
     ap.add_argument("--profile", action="store_true", help="run the small ncu case only")
     ap.add_argument("--profile-updates", type=int, default=20)
     ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1"])
+    ap.add_argument("--serve", action="store_true", help="run the serving workload only")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-step", type=int, default=20)
     args = ap.parse_args()
-    if args.profile:
+    if args.serve:
+        run_serving(args)
+    elif args.profile:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

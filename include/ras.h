@@ -152,6 +152,50 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
                            double *const *x, double tol, int32_t mode, int64_t max_updates,
                            ras_solve_info *infos);
 
+/* Choice made by ras_autotune. */
+typedef struct {
+  int32_t cta_threads;  /* threads per CTA of the persistent kernel */
+  int32_t staged;       /* 1: local matrix staged in shared memory (FP32 CG) */
+  int32_t inner_iters;  /* CG / PCG steps per local solve */
+  int32_t candidates;   /* configurations timed */
+  double score;         /* best -ln(relres) per kernel millisecond */
+} ras_tune_result;
+
+/* Launch-shape autotuner (not in the paper: the GPU counterpart of choosing
+ * the local solver's parameters). Times `iters` updates of the real system
+ * (b DEVICE; x_scratch DEVICE double[n], overwritten) for each candidate - CTA
+ * threads 256 / 512 for CG and ILU-PCG, the shared-memory staged FP32 CG, and
+ * with tune_inner != 0 the inner step counts m/2, m, 2m - and keeps the one
+ * with the largest residual reduction per millisecond of kernel time. The
+ * context then uses it for every solve. out may be NULL. */
+ras_status ras_autotune(ras_ctx *ctx, const double *b, double *x_scratch, int32_t mode,
+                        int32_t iters, int32_t tune_inner, ras_tune_result *out);
+
+/* ------------------------------------------------------------------------ */
+/* Continuous batching (serving)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Starts a solve on ctx without running it: records b, x (DEVICE, x holds
+ * the initial guess) and tol, and initialises the solve state on the
+ * context's stream (||b||^2 over every Omega_p and O_p, counters, the async
+ * phase word). The context then advances only through ras_batch_step, which
+ * may run it together with other contexts. */
+ras_status ras_solve_begin(ras_ctx *ctx, const double *b, double *x, double tol);
+
+/* Advances every listed context - each started with ras_solve_begin - in ONE
+ * persistent launch (the batched launch of the subdomains of all systems, as
+ * in ras_solve_batch) by at most step_limit local updates per subdomain
+ * (RAS_ASYNC: the asynchronous solver of Sec. 2.1 with its convergence
+ * detection, Sec. 3.3.2) or step_limit iterations (RAS_SYNC). Systems that
+ * finished earlier are skipped. Between steps each x holds the current
+ * iterate. Issued on the stream of ctxs[0] after the streams of the others.
+ * done (HOST int32[num], may be NULL): 1 for systems finished (converged or
+ * failed) by the end of this step. infos (HOST, may be NULL): filled for
+ * finished systems. max_updates as in ras_solve. Returns the first non-OK
+ * status among finished systems, or a launch error. */
+ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64_t step_limit,
+                          int64_t max_updates, int32_t *done, ras_solve_info *infos);
+
 /* Releases a context (NULL is allowed). Synchronises its stream first. */
 ras_status ras_destroy(ras_ctx *ctx);
 
@@ -174,6 +218,14 @@ ras_status ras_get_info(const ras_ctx *ctx, int32_t *num_parts, int32_t *n, int3
 
 /* Per-subdomain local-update counts of the last solve: counts[num_parts]. */
 ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
+
+/* Runtime breakdown of the last solve, per subdomain (the per-update timing
+ * of Sec. 4's Figs. 3a-7a): ns[3*p+0] nanoseconds spent gathering the local
+ * residual (reading neighbours' values), ns[3*p+1] in the local solve,
+ * ns[3*p+2] in the restricted update and publish, summed over all updates of
+ * subdomain p (device %globaltimer, measured by the CTA that ran it).
+ * ns: HOST uint64[3 * num_parts]. RAS_EINVAL before the first solve. */
+ras_status ras_get_phase_times(const ras_ctx *ctx, uint64_t *ns);
 
 /* FP64 global relative residual ||b - A x|| / ||b|| computed on the device
  * (b, x DEVICE). Synchronises the context's stream. */

@@ -49,10 +49,19 @@ class ras_solve_info(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class ras_tune_result(C.Structure):
+    _fields_ = [("cta_threads", C.c_int32), ("staged", C.c_int32), ("inner_iters", C.c_int32),
+                ("candidates", C.c_int32), ("score", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RasError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, info=None):
         super().__init__(f"{where}: {ras_status_str(status)} (status {status})")
         self.status = status
+        self.info = info  # ras_solve_info of a failed solve, when there is one
 
 
 def lib_path() -> str:
@@ -85,6 +94,10 @@ def load():
             "ras_get_update_counts": ([P, P], C.c_int),
             "ras_relres": ([P, P, P, C.POINTER(D)], C.c_int),
             "ras_relres_noalloc": ([I32, P, P, P, P, P, P, P], C.c_int),
+            "ras_solve_begin": ([P, P, P, D], C.c_int),
+            "ras_get_phase_times": ([P, P], C.c_int),
+            "ras_autotune": ([P, P, P, I32, I32, I32, C.POINTER(ras_tune_result)], C.c_int),
+            "ras_batch_step": ([P, I32, I32, I64, I64, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -187,8 +200,10 @@ def ras_solve(ctx: RasContext, b, x, tol: float = 1e-8, mode: int = RAS_SYNC,
     """Solves A x = b on the device; x holds x0 on entry. Raises RasError on
     failure except RAS_ENOCONV, which is reported in info.status."""
     info = ras_solve_info()
-    _check(load().ras_solve(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x, ctx.n, "x"), tol, mode,
-                            max_updates, C.byref(info)), "ras_solve", allow=(RAS_ENOCONV,))
+    st = load().ras_solve(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x, ctx.n, "x"), tol, mode,
+                          max_updates, C.byref(info))
+    if st not in (RAS_OK, RAS_ENOCONV):
+        raise RasError(st, "ras_solve", info)
     return info
 
 
@@ -216,6 +231,32 @@ def ras_solve_batch(ctxs, bs, xs, tol: float = 1e-8, mode: int = RAS_SYNC, max_u
     _check(load().ras_solve_batch(cp, num, bp, xp, tol, mode, max_updates, infos),
            "ras_solve_batch", allow=(RAS_ENOCONV,))
     return list(infos)
+
+
+def ras_autotune(ctx: RasContext, b, x_scratch, mode: int = RAS_SYNC, iters: int = 20,
+                 tune_inner: bool = True) -> ras_tune_result:
+    """Times candidate launch shapes / inner step counts and keeps the best."""
+    out = ras_tune_result()
+    _check(load().ras_autotune(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x_scratch, ctx.n, "x"), mode,
+                               iters, 1 if tune_inner else 0, C.byref(out)), "ras_autotune")
+    return out
+
+
+def ras_solve_begin(ctx: RasContext, b, x, tol: float = 1e-8) -> None:
+    """Starts a solve (continuous batching); advance it with ras_batch_step."""
+    _check(load().ras_solve_begin(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x, ctx.n, "x"), tol),
+           "ras_solve_begin")
+
+
+def ras_batch_step(ctxs, mode: int = RAS_ASYNC, step_limit: int = 50, max_updates: int = 0):
+    """One batched step over the begun contexts; returns (done flags, infos)."""
+    num = len(ctxs)
+    cp = (C.c_void_p * num)(*[c.ptr for c in ctxs])
+    done = np.zeros(num, dtype=np.int32)
+    infos = (ras_solve_info * num)()
+    _check(load().ras_batch_step(cp, num, mode, step_limit, max_updates, done.ctypes.data, infos),
+           "ras_batch_step", allow=(RAS_ENOCONV,))
+    return done.astype(bool), list(infos)
 
 
 def ras_destroy(ctx: RasContext) -> None:
@@ -251,6 +292,13 @@ def ras_get_update_counts(ctx: RasContext) -> np.ndarray:
     out = np.zeros(ctx.num_parts, dtype=np.int64)
     _check(load().ras_get_update_counts(ctx.ptr, out.ctypes.data), "ras_get_update_counts")
     return out
+
+
+def ras_get_phase_times(ctx: RasContext) -> np.ndarray:
+    """(num_parts, 3) nanoseconds in gather / local solve / update of the last solve."""
+    out = np.zeros(3 * ctx.num_parts, dtype=np.uint64)
+    _check(load().ras_get_phase_times(ctx.ptr, out.ctypes.data), "ras_get_phase_times")
+    return out.reshape(ctx.num_parts, 3)
 
 
 def ras_relres(ctx: RasContext, b, x) -> float:

@@ -125,7 +125,7 @@ struct DevBuf {
 };
 
 struct LaunchPlan {
-  int nt = 0, grid = 0, kmax = 0;
+  int nt = 0, grid = 0, kmax = 0, nstages = 4;
   size_t smem = 0;
   int Wmax = 0, npad_max = 0;
   std::vector<Item> items;
@@ -149,6 +149,7 @@ struct ras_ctx {
   ras_local_solver ls{};
   int maxw = 0;  // largest true local half-bandwidth
   int exec_kind = 0;  // kernel variant (LocalKind; kCGS for staged FP32 CG)
+  int nt_pref = 0;    // preferred CTA threads of the CG / ILU variants (0: default)
   // host copies of the maps (inspection)
   std::vector<std::vector<int32_t>> omega, iface;
   std::vector<std::vector<uint8_t>> owned;
@@ -163,7 +164,7 @@ struct ras_ctx {
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
   uint8_t *d_ownf = nullptr;
-  double *d_rval = nullptr, *d_xalt = nullptr;
+  double *d_rval = nullptr, *d_xalt = nullptr, *d_xg = nullptr;
   void *d_fac = nullptr, *d_lval = nullptr, *d_lu = nullptr;
   int64_t device_bytes = 0;
   // launch state
@@ -175,8 +176,15 @@ struct ras_ctx {
   SysState *h_st = nullptr;
   SubState *h_sub = nullptr;
   double *d_bx = nullptr;  // device b and x for ras_solve_host
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr, ev_begin = nullptr;
+  bool begun = false, finished = false;  // continuous-batching state
+  uint64_t serial = next_serial();       // identity that survives address reuse
+  static uint64_t next_serial() {
+    static std::atomic<uint64_t> n(1);
+    return n.fetch_add(1);
+  }
   std::vector<int64_t> last_updates;
+  std::vector<uint64_t> last_phase;  // 3 per subdomain: gather, solve, update ns
 
   template <typename T>
   ras_status alloc(T *&ptr, size_t count) {
@@ -218,6 +226,7 @@ struct ras_ctx {
     if (ev1) cudaEventDestroy(ev1);
     if (evk0) cudaEventDestroy(evk0);
     if (evk1) cudaEventDestroy(evk1);
+    if (ev_begin) cudaEventDestroy(ev_begin);
   }
 };
 
@@ -438,18 +447,19 @@ void assign_items(LaunchPlan &pl, const std::vector<Item> &items, const std::vec
 
 ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Item> &items,
                        const std::vector<double> &cost, int Wmax, int npad_max, int kmax,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int nt_pref = 0) {
   pl.release();
   int dev = 0, nsm = 0, max_smem = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int nt_pref = (int)env_int("RAS_CTA_THREADS", 256);
+  if (nt_pref <= 0) nt_pref = (int)env_int("RAS_CTA_THREADS", 256);
   pl.nt = main_threads(kind, nt_pref);
   pl.Wmax = Wmax;
   pl.npad_max = npad_max;
   pl.kmax = kmax;
-  pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax);
+  pl.nstages = (int)std::min<int64_t>(8, std::max<int64_t>(2, env_int("RAS_BAND_STAGES", 4)));
+  pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax, pl.nstages);
   if (pl.smem + 4096 > (size_t)max_smem) return RAS_ENOTSUP;
   const int occ = main_occupancy(kind, prec, pl.nt, pl.smem);
   if (occ <= 0) return RAS_ENOTSUP;
@@ -489,6 +499,7 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.rcol = c->d_rcol;
   s.rval = c->d_rval;
   s.own_l = c->d_own;
+  s.xg = c->d_xg;
   s.fac = c->d_fac;
   s.lcol = c->d_lcol;
   s.lcol16 = c->d_lcol16;
@@ -822,6 +833,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   CUDA_TRY(cudaEventCreate(&c->ev1));
   CUDA_TRY(cudaEventCreate(&c->evk0));
   CUDA_TRY(cudaEventCreate(&c->evk1));
+  CUDA_TRY(cudaEventCreateWithFlags(&c->ev_begin, cudaEventDisableTiming));
   if ((st = c->upload(c->d_subs, c->subs)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_sub, P)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_st, 1)) != RAS_OK) return st;
@@ -832,6 +844,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   if ((st = c->upload(c->d_own, own)) != RAS_OK) return st;
   if ((st = c->upload(c->d_nbr, nbr)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_xalt, n)) != RAS_OK) return st;
+  if ((st = c->alloc(c->d_xg, (size_t)rows)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_ctl, 1)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_sysdesc, 1)) != RAS_OK) return st;
   CUDA_TRY(cudaMallocHost(&c->h_sysdesc, sizeof(SysDesc)));
@@ -900,7 +913,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   } else {
     std::vector<int32_t> &lc = lcol;
     if ((st = c->upload(c->d_lcol, lc)) != RAS_OK) return st;
-    if (c->exec_kind == kCGS) {
+    if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && npad_max <= kStagedRows) {
       std::vector<int16_t> l16(lc.begin(), lc.end());
       if ((st = c->upload(c->d_lcol16, l16)) != RAS_OK) return st;
     }
@@ -963,6 +976,7 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.npad_max = pl.npad_max;
   L.persist = 1;
   L.kmax = pl.kmax;
+  L.nstages = pl.nstages;
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   const int nitems = (int)pl.items.size();
@@ -985,9 +999,13 @@ ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const
   else if (st.status != 0) rs = (ras_status)st.status;
   std::vector<int64_t> u(c->P);
   int64_t stale = 0;
+  c->last_phase.assign(3 * (size_t)c->P, 0);
   for (int p = 0; p < c->P; ++p) {
     u[p] = sub[p].updates;
     stale += sub[p].stale;
+    c->last_phase[3 * p] = sub[p].t_gather;
+    c->last_phase[3 * p + 1] = sub[p].t_solve;
+    c->last_phase[3 * p + 2] = sub[p].t_update;
   }
   c->last_updates = u;
   if (info) {
@@ -1129,6 +1147,244 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
   return first;
 }
 
+ras_status ras_solve_begin(ras_ctx *c, const double *b, double *x, double tol) {
+  if (!c || !b || !x || !(tol > 0.0)) return RAS_EINVAL;
+  *c->h_sysdesc = make_sysdesc(c, b, x, tol);
+  CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
+                           c->stream));
+  Launch L{};
+  L.sys = c->d_sysdesc;
+  L.nsys = 1;
+  L.items = c->plan.d_items;
+  CUDA_TRY(launch_init(L, (int)c->plan.items.size(), c->stream));
+  CUDA_TRY(cudaEventRecord(c->ev_begin, c->stream));
+  c->begun = true;
+  c->finished = false;
+  return RAS_OK;
+}
+
+namespace {
+
+// Launch plan and device buffers of the last batch step on this host thread;
+// reused while the same contexts, in the same order, are stepped.
+struct StepCache {
+  std::vector<uint64_t> key;  // serials of the stepped contexts, in order
+  LaunchPlan plan;
+  SysDesc *d_sys = nullptr;
+  GridCtl *d_ctl = nullptr;
+  SysDesc *h_sys = nullptr;  // pinned
+  GridCtl *h_ctl = nullptr;  // pinned
+  SysState *h_st = nullptr;  // pinned
+  int cap = 0;
+  void release() {
+    plan.release();
+    cudaFree(d_sys);
+    cudaFree(d_ctl);
+    cudaFreeHost(h_sys);
+    cudaFreeHost(h_ctl);
+    cudaFreeHost(h_st);
+    d_sys = nullptr;
+    d_ctl = nullptr;
+    h_sys = nullptr;
+    h_ctl = nullptr;
+    h_st = nullptr;
+    cap = 0;
+    key.clear();
+  }
+  ~StepCache() { release(); }
+};
+thread_local StepCache g_step;
+
+}  // namespace
+
+ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64_t step_limit,
+                          int64_t max_updates, int32_t *done, ras_solve_info *infos) {
+  if (!ctxs || num <= 0 || step_limit <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
+    return RAS_EINVAL;
+  for (int s = 0; s < num; ++s) {
+    if (!ctxs[s] || !ctxs[s]->begun || ctxs[s]->exec_kind != ctxs[0]->exec_kind ||
+        ctxs[s]->ls.prec != ctxs[0]->ls.prec || ctxs[s]->ls.inner_iters != ctxs[0]->ls.inner_iters)
+      return RAS_EINVAL;
+    for (int t = 0; t < s; ++t)
+      if (ctxs[t] == ctxs[s]) return RAS_EINVAL;
+  }
+  ras_ctx *c0 = ctxs[0];
+  cudaStream_t stream = c0->stream;
+  StepCache &sc = g_step;
+  std::vector<uint64_t> key(num);
+  for (int s = 0; s < num; ++s) key[s] = ctxs[s]->serial;
+  if (key != sc.key) {
+    sc.release();
+    std::vector<Item> items;
+    std::vector<double> cost;
+    int Wmax = 0, npad_max = 0, kmax = 0;
+    for (int s = 0; s < num; ++s) {
+      ras_ctx *c = ctxs[s];
+      for (int p = 0; p < c->P; ++p) {
+        items.push_back({s, p, 0, 0});
+        cost.push_back(c->cost[p]);
+      }
+      Wmax = std::max(Wmax, c->plan.Wmax);
+      npad_max = std::max(npad_max, c->plan.npad_max);
+      kmax = std::max(kmax, c->K);
+    }
+    ras_status rs = plan_launch(sc.plan, c0->exec_kind, c0->ls.prec, items, cost, Wmax, npad_max,
+                                kmax, stream);
+    if (rs != RAS_OK) {
+      sc.release();
+      return rs;
+    }
+    if (cudaMalloc(&sc.d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+        cudaMalloc(&sc.d_ctl, sizeof(GridCtl)) != cudaSuccess ||
+        cudaMallocHost(&sc.h_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+        cudaMallocHost(&sc.h_ctl, sizeof(GridCtl)) != cudaSuccess ||
+        cudaMallocHost(&sc.h_st, sizeof(SysState) * num) != cudaSuccess) {
+      sc.release();
+      return RAS_ENOMEM;
+    }
+    sc.cap = num;
+    sc.key = key;
+  }
+  int running = 0;
+  for (int s = 0; s < num; ++s) {
+    sc.h_sys[s] = *ctxs[s]->h_sysdesc;
+    if (!ctxs[s]->finished) ++running;
+    if (ctxs[s]->stream != stream) CUDA_TRY(cudaStreamWaitEvent(stream, ctxs[s]->ev_begin, 0));
+  }
+  CUDA_TRY(cudaMemcpyAsync(sc.d_sys, sc.h_sys, sizeof(SysDesc) * num, cudaMemcpyHostToDevice,
+                           stream));
+  Launch L{};
+  L.sys = sc.d_sys;
+  L.nsys = num;
+  L.mode = mode;
+  L.items = sc.plan.d_items;
+  L.cta_off = sc.plan.d_cta_off;
+  L.cta_sys = sc.plan.d_cta_sys;
+  L.cta_sys_off = sc.plan.d_cta_sys_off;
+  L.ctl = sc.d_ctl;
+  L.max_updates = max_updates > 0 ? max_updates : 1000000;
+  L.step_limit = step_limit;
+  L.timeout_ns = timeout_ns();
+  L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
+  L.max_restarts = 8;
+  L.m = c0->ls.inner_iters;
+  L.Wmax = sc.plan.Wmax;
+  L.npad_max = sc.plan.npad_max;
+  L.persist = 0;
+  L.kmax = sc.plan.kmax;
+  L.nstages = sc.plan.nstages;
+  std::memset(sc.h_ctl, 0, sizeof(GridCtl));
+  sc.h_ctl->remaining = running;
+  const int nitems = (int)sc.plan.items.size();
+  CUDA_TRY(cudaMemcpyAsync(sc.d_ctl, sc.h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(launch_main(c0->exec_kind, c0->ls.prec, sc.plan.nt, L, sc.plan.grid, sc.plan.smem,
+                       stream));
+  if (mode == RAS_SYNC) CUDA_TRY(launch_copyback(L, nitems, stream));
+  CUDA_TRY(launch_residual(L, nitems, stream));
+  for (int s = 0; s < num; ++s)
+    CUDA_TRY(cudaMemcpyAsync(&sc.h_st[s], ctxs[s]->d_st, sizeof(SysState), cudaMemcpyDeviceToHost,
+                             stream));
+  CUDA_TRY(cudaMemcpyAsync(sc.h_ctl, sc.d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  ras_status first = sc.h_ctl->status != 0 ? (ras_status)sc.h_ctl->status : RAS_OK;
+  std::vector<int> newly;
+  for (int s = 0; s < num; ++s) {
+    const SysState &st = sc.h_st[s];
+    const bool fin = mode == RAS_SYNC ? st.done != 0 : (st.word & 3u) == (uint32_t)kDone;
+    if (fin && !ctxs[s]->finished) newly.push_back(s);
+    if (fin) ctxs[s]->finished = true;
+    if (done) done[s] = ctxs[s]->finished ? 1 : 0;
+  }
+  for (int s : newly) {
+    ras_ctx *c = ctxs[s];
+    CUDA_TRY(cudaMemcpyAsync(c->h_sub, c->d_sub, sizeof(SubState) * c->P, cudaMemcpyDeviceToHost,
+                             stream));
+  }
+  if (!newly.empty()) CUDA_TRY(cudaStreamSynchronize(stream));
+  for (int s : newly) {
+    ras_ctx *c = ctxs[s];
+    ras_solve_info tmp{};
+    ras_status r = finish_info(c, sc.h_st[s], *sc.h_ctl, c->h_sub, mode, &tmp, 0.f, 0.f);
+    if (infos) infos[s] = tmp;
+    if (first == RAS_OK && r != RAS_OK) first = r;
+  }
+  return first;
+}
+
+ras_status ras_autotune(ras_ctx *c, const double *b, double *x_scratch, int32_t mode,
+                        int32_t iters, int32_t tune_inner, ras_tune_result *out) {
+  if (!c || !b || !x_scratch || iters <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
+    return RAS_EINVAL;
+  struct Cand {
+    int exec_kind, nt, m;
+  };
+  std::vector<Cand> cands;
+  const int kind = c->ls.kind, prec = c->ls.prec, m0 = c->ls.inner_iters;
+  std::vector<int> ms = {m0};
+  if (tune_inner && kind != RAS_LOCAL_BANDCHOL) {
+    ms.push_back(std::max(1, m0 / 2));
+    ms.push_back(2 * m0);
+  }
+  for (int m : ms) {
+    if (kind == RAS_LOCAL_BANDCHOL) {
+      cands.push_back({kBand, 256, m});
+    } else {
+      cands.push_back({kind, 256, m});
+      cands.push_back({kind, 512, m});
+      if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && c->d_lcol16) cands.push_back({kCGS, 512, m});
+    }
+  }
+  std::vector<Item> items(c->P);
+  for (int p = 0; p < c->P; ++p) items[p] = {0, p, 0, 0};
+  const Cand saved = {c->exec_kind, c->nt_pref, m0};
+  double best = -1.0;
+  Cand pick = saved;
+  int tried = 0;
+  for (const Cand &cd : cands) {
+    LaunchPlan pl;
+    if (plan_launch(pl, cd.exec_kind, prec, items, c->cost, c->plan.Wmax, c->plan.npad_max, c->K,
+                    c->stream, cd.nt) != RAS_OK) {
+      pl.release();
+      continue;
+    }
+    std::swap(pl, c->plan);
+    const int ek = c->exec_kind;
+    c->exec_kind = cd.exec_kind;
+    c->ls.inner_iters = cd.m;
+    CUDA_TRY(cudaMemsetAsync(x_scratch, 0, sizeof(double) * c->n, c->stream));
+    ras_solve_info info{};
+    ras_status rs = ras_solve(c, b, x_scratch, 1e-300, mode, iters, &info);
+    std::swap(pl, c->plan);
+    c->exec_kind = ek;
+    pl.release();
+    if (rs != RAS_OK && rs != RAS_ENOCONV) continue;
+    ++tried;
+    // residual reduction per millisecond (relres starts at 1 from x0 = 0)
+    const double red = -std::log(std::max(info.relres, 1e-300));
+    const double score = red / std::max(info.kernel_ms, 1e-6);
+    if (score > best) {
+      best = score;
+      pick = cd;
+    }
+  }
+  c->ls.inner_iters = pick.m;
+  c->exec_kind = pick.exec_kind;
+  c->nt_pref = pick.nt;
+  if (pick.exec_kind != saved.exec_kind || pick.nt != saved.nt) {
+    ras_status st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax,
+                                c->plan.npad_max, c->K, c->stream, c->nt_pref);
+    if (st != RAS_OK) return st;
+  }
+  if (out) {
+    out->cta_threads = c->plan.nt;
+    out->staged = c->exec_kind == kCGS ? 1 : 0;
+    out->inner_iters = c->ls.inner_iters;
+    out->candidates = tried;
+    out->score = best;
+  }
+  return tried > 0 ? RAS_OK : RAS_ENOTSUP;
+}
+
 ras_status ras_get_maps(const ras_ctx *c, int32_t p, const int32_t **omega, int32_t *n_omega,
                         const uint8_t **owned_mask, const int32_t **iface, int32_t *n_iface) {
   if (!c || p < 0 || p >= c->P || !omega || !n_omega || !owned_mask || !iface || !n_iface)
@@ -1154,6 +1410,13 @@ ras_status ras_get_info(const ras_ctx *c, int32_t *num_parts, int32_t *n, int32_
 ras_status ras_get_update_counts(const ras_ctx *c, int64_t *counts) {
   if (!c || !counts) return RAS_EINVAL;
   std::copy(c->last_updates.begin(), c->last_updates.end(), counts);
+  return RAS_OK;
+}
+
+ras_status ras_get_phase_times(const ras_ctx *c, uint64_t *ns) {
+  if (!c || !ns) return RAS_EINVAL;
+  if (c->last_phase.size() != 3 * (size_t)c->P) return RAS_EINVAL;
+  std::copy(c->last_phase.begin(), c->last_phase.end(), ns);
   return RAS_OK;
 }
 

@@ -51,6 +51,9 @@ struct SubState {
   int64_t updates;    // local solves in the current solve
   int64_t step_updates;  // local solves in the current launch
   int64_t stale;      // async: solves that saw no new neighbour data
+  uint64_t t_gather;  // accumulated ns in the residual gather
+  uint64_t t_solve;   // accumulated ns in the local solve
+  uint64_t t_update;  // accumulated ns in the restricted update + publish
   uint64_t nbr_seen;  // async: sum of neighbour versions at the last solve
   uint32_t version;   // async: published update counter (release store)
   int32_t conv_epoch; // async: epoch in which Eq. 2 last held (-1: not converged)
@@ -89,6 +92,7 @@ struct SysDesc {
   const int32_t *rcol;
   const double *rval;
   const int32_t *own_l;
+  double *xg;    // per local row: the x value the last gather used (owned rows)
   const void *fac;
   const int32_t *lcol;
   const int16_t *lcol16;  // local columns as int16 (staged CG)
@@ -139,6 +143,8 @@ struct Launch {
   int32_t npad_max;
   int32_t persist;             // async: keep polling until every system is done
   int32_t kmax;                // largest ELL width over the launch
+  int32_t nstages;             // band: slab ring depth (2..8)
+  int32_t pad2_;
 };
 
 }  // namespace ras

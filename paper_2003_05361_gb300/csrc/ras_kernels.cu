@@ -103,6 +103,21 @@ __device__ __forceinline__ V block_sum(V v, V *red) {
   return s;
 }
 
+// Same deterministic sum with a single barrier: callers alternate between two
+// buffers, so a buffer is rewritten only after every thread has passed the
+// barrier of the reduction in between.
+template <int NT, typename V>
+__device__ __forceinline__ V block_sum_1b(V v, V *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  V s = red[0];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
 template <int NT>
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
 #pragma unroll
@@ -415,6 +430,7 @@ __global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
     s.step_updates = 0;
     s.stale = 0;
     s.nbr_seen = 0;
+    s.t_gather = s.t_solve = s.t_update = 0;
     s.version = 0;
     s.conv_epoch = -1;
     s.park_epoch = -1;
@@ -524,7 +540,10 @@ template <> struct Vec16<__nv_bfloat16> {
 
 // One forward block (lane l, row i = 32K + l): c = r_i - sum_{t < W-l} F[l][t] y[i-W+t],
 // then y_i = sum_{m <= l} Linv[l][m] c_m. `row` is this lane's slab row, y is
-// indexed so that y[0] is global row 0.
+// indexed so that y[0] is global row 0. Every shared load below is in bounds
+// and reads finite data (slab rows, zero-padded y, cbuf), so out-of-range
+// terms are removed with selects instead of predicated loads, which lets the
+// unrolled loops issue their loads ahead of the FMAs.
 template <typename T, typename CT>
 __device__ __forceinline__ void band_fwd_block(const T *row, CT *y, int i, int W, int lane,
                                                CT *cbuf) {
@@ -533,48 +552,60 @@ __device__ __forceinline__ void band_fwd_block(const T *row, CT *y, int i, int W
   const CT *yb = y + i - W;
   CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
   const int tfull = ((W - 31) / V) * V;  // t < tfull: every lane is off-block
+#pragma unroll 4
   for (int t = 0; t < tfull; t += V) {
     CT v[V];
     VL::load(row + t, v);
 #pragma unroll
-    for (int u = 0; u < V; u += 4) {
-      a0 -= v[u] * yb[t + u];
-      if (u + 1 < V) a1 -= v[u + 1] * yb[t + u + 1];
-      if (u + 2 < V) a2 -= v[u + 2] * yb[t + u + 2];
-      if (u + 3 < V) a3 -= v[u + 3] * yb[t + u + 3];
+    for (int u = 0; u < V; ++u) {
+      const CT pr = v[u] * yb[t + u];
+      if ((u & 3) == 0) a0 -= pr;
+      else if ((u & 3) == 1) a1 -= pr;
+      else if ((u & 3) == 2) a2 -= pr;
+      else a3 -= pr;
     }
   }
   const int lim = W - lane;
+#pragma unroll 4
   for (int t = tfull; t < W; t += V) {
     CT v[V];
     VL::load(row + t, v);
 #pragma unroll
-    for (int u = 0; u < V; ++u)
-      if (t + u < lim) {
-        const CT pr = v[u] * yb[t + u];
-        if ((u & 3) == 0) a0 -= pr;
-        else if ((u & 3) == 1) a1 -= pr;
-        else if ((u & 3) == 2) a2 -= pr;
-        else a3 -= pr;
-      }
+    for (int u = 0; u < V; ++u) {
+      const CT pr = (t + u < lim) ? v[u] * yb[t + u] : CT(0);
+      if ((u & 3) == 0) a0 -= pr;
+      else if ((u & 3) == 1) a1 -= pr;
+      else if ((u & 3) == 2) a2 -= pr;
+      else a3 -= pr;
+    }
   }
   cbuf[lane] = (a0 + a1) + (a2 + a3);
   __syncwarp();
-  const T *rb = row + W - lane;  // rb[m] = Linv[lane][m]
+  const T *rb = row + W - lane;  // rb[m] = Linv[lane][m] for m <= lane
   CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
 #pragma unroll
   for (int m = 0; m < 32; m += 4) {
-    if (m <= lane) b0 += to_ct(rb[m]) * cbuf[m];
-    if (m + 1 <= lane) b1 += to_ct(rb[m + 1]) * cbuf[m + 1];
-    if (m + 2 <= lane) b2 += to_ct(rb[m + 2]) * cbuf[m + 2];
-    if (m + 3 <= lane) b3 += to_ct(rb[m + 3]) * cbuf[m + 3];
+    CT c4[4];
+    if constexpr (sizeof(CT) == 4) {
+      const float4 cv = *reinterpret_cast<const float4 *>(cbuf + m);
+      c4[0] = cv.x; c4[1] = cv.y; c4[2] = cv.z; c4[3] = cv.w;
+    } else {
+      const double2 c01 = *reinterpret_cast<const double2 *>(cbuf + m);
+      const double2 c23 = *reinterpret_cast<const double2 *>(cbuf + m + 2);
+      c4[0] = c01.x; c4[1] = c01.y; c4[2] = c23.x; c4[3] = c23.y;
+    }
+    b0 += (m <= lane) ? to_ct(rb[m]) * c4[0] : CT(0);
+    b1 += (m + 1 <= lane) ? to_ct(rb[m + 1]) * c4[1] : CT(0);
+    b2 += (m + 2 <= lane) ? to_ct(rb[m + 2]) * c4[2] : CT(0);
+    b3 += (m + 3 <= lane) ? to_ct(rb[m + 3]) * c4[3] : CT(0);
   }
   y[i] = (b0 + b1) + (b2 + b3);
   __syncwarp();
 }
 
 // One backward block: c = y_i - sum_{32-l <= d <= W} B[l][d] z[i+d], then
-// z_i = sum_{d <= 31-l} Uinv[l][l+d] c_{l+d}.
+// z_i = sum_{d <= 31-l} Uinv[l][l+d] c_{l+d}. cbuf has 64 entries, the upper
+// 32 zero, so cbuf[l + d] is in bounds for every d < 32.
 template <typename T, typename CT>
 __device__ __forceinline__ void band_bwd_block(const T *row, CT *y, int i, int W, int lane,
                                                CT *cbuf) {
@@ -583,29 +614,32 @@ __device__ __forceinline__ void band_bwd_block(const T *row, CT *y, int i, int W
   const CT *zb = y + i;
   CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
   const int d0 = 32 - lane;
+#pragma unroll
   for (int d = 0; d < 32; d += V) {
     CT v[V];
     VL::load(row + d, v);
 #pragma unroll
-    for (int u = 0; u < V; ++u)
-      if (d + u >= d0 && d + u <= W) {
-        const CT pr = v[u] * zb[d + u];
-        if ((u & 3) == 0) a0 -= pr;
-        else if ((u & 3) == 1) a1 -= pr;
-        else if ((u & 3) == 2) a2 -= pr;
-        else a3 -= pr;
-      }
+    for (int u = 0; u < V; ++u) {
+      const CT pr = (d + u >= d0 && d + u <= W) ? v[u] * zb[d + u] : CT(0);
+      if ((u & 3) == 0) a0 -= pr;
+      else if ((u & 3) == 1) a1 -= pr;
+      else if ((u & 3) == 2) a2 -= pr;
+      else a3 -= pr;
+    }
   }
-  // d in [32, S): slab entries beyond W are zero, z beyond the subdomain is zero
+  // d in [32, W]: entries of the last chunk beyond W are zero in the slab and
+  // z beyond the subdomain is zero
+#pragma unroll 4
   for (int d = 32; d <= W; d += V) {
     CT v[V];
     VL::load(row + d, v);
 #pragma unroll
-    for (int u = 0; u < V; u += 4) {
-      a0 -= v[u] * zb[d + u];
-      if (u + 1 < V) a1 -= v[u + 1] * zb[d + u + 1];
-      if (u + 2 < V) a2 -= v[u + 2] * zb[d + u + 2];
-      if (u + 3 < V) a3 -= v[u + 3] * zb[d + u + 3];
+    for (int u = 0; u < V; ++u) {
+      const CT pr = v[u] * zb[d + u];
+      if ((u & 3) == 0) a0 -= pr;
+      else if ((u & 3) == 1) a1 -= pr;
+      else if ((u & 3) == 2) a2 -= pr;
+      else a3 -= pr;
     }
   }
   cbuf[lane] = (a0 + a1) + (a2 + a3);
@@ -616,17 +650,129 @@ __device__ __forceinline__ void band_bwd_block(const T *row, CT *y, int i, int W
     CT v[V];
     VL::load(row + d, v);
 #pragma unroll
-    for (int u = 0; u < V; ++u)
-      if (d + u < 32 - lane) {
-        const CT pr = v[u] * cbuf[lane + d + u];
-        if ((u & 3) == 0) b0 += pr;
-        else if ((u & 3) == 1) b1 += pr;
-        else if ((u & 3) == 2) b2 += pr;
-        else b3 += pr;
-      }
+    for (int u = 0; u < V; ++u) {
+      const CT pr = (d + u < 32 - lane) ? v[u] * cbuf[lane + d + u] : CT(0);
+      if ((u & 3) == 0) b0 += pr;
+      else if ((u & 3) == 1) b1 += pr;
+      else if ((u & 3) == 2) b2 += pr;
+      else b3 += pr;
+    }
   }
   y[i] = (b0 + b1) + (b2 + b3);
   __syncwarp();
+}
+
+// Banded Cholesky solve L L^T delta = r by the whole CTA (NT threads, NW =
+// NT/32 warps). For each 32-row block the off-block dot products (the part
+// that reads earlier / later blocks) are split over the warps by column
+// slices; warp 0 adds the NW partials in a fixed order, applies the inverse
+// diagonal block and publishes the 32 new values; two CTA barriers per block.
+// y[i] (local row i) holds r on entry and delta on exit; y[-W, 0) and
+// y[npad, npad+W+16) must be zero. Slabs stream through an NS-stage ring with
+// bulk copies issued by thread 0, up to NS blocks ahead.
+template <typename T, typename CT, int NT>
+__device__ bool band_solve_cta(const T *slabF, const T *slabB, int nb, int W, CT *y, CT *cbuf,
+                               CT *part, T *ring, int ring_stride, uint64_t *mbar,
+                               uint32_t &gcount, int64_t timeout_ns, const int NS) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = slab_stride(W, (int)sizeof(T));
+  const int64_t slab = (int64_t)32 * S;
+  const uint32_t bytes = (uint32_t)(slab * sizeof(T));
+  const int tw = (W + NW - 1) / NW;  // columns per warp slice
+  for (int dir = 0; dir < 2; ++dir) {
+    const T *base = dir == 0 ? slabF : slabB;
+    const int pro = nb < NS ? nb : NS;
+    if (tid == 0)
+      for (int j = 0; j < pro; ++j) {
+        const int Kb = dir == 0 ? j : nb - 1 - j;
+        const uint32_t st = (gcount + j) % NS;
+        fence_proxy_async();
+        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
+      }
+    for (int s = 0; s < nb; ++s) {
+      const uint32_t g = gcount + s;
+      const uint32_t st = g % NS;
+      const bool ok = mbar_wait(&mbar[st], (g / NS) & 1u, timeout_ns);
+      const T *row = ring + st * ring_stride + lane * S;
+      const int K = dir == 0 ? s : nb - 1 - s;
+      const int i = 32 * K + lane;
+      // off-block partial of this warp's column slice
+      CT a0 = CT(0), a1 = CT(0);
+      const int c0 = warp * tw;
+      const int c1 = c0 + tw < W ? c0 + tw : W;
+      if (!ok) {
+        // slab never arrived: contribute nothing, fail at the barrier below
+      } else if (dir == 0) {
+        const int lim = W - lane;  // t < lim: columns left of the block
+        const CT *yb = y + i - W;
+        int t = c0;
+        for (; t + 1 < c1; t += 2) {
+          a0 += (t < lim) ? to_ct(row[t]) * yb[t] : CT(0);
+          a1 += (t + 1 < lim) ? to_ct(row[t + 1]) * yb[t + 1] : CT(0);
+        }
+        if (t < c1) a0 += (t < lim) ? to_ct(row[t]) * yb[t] : CT(0);
+      } else {
+        const int d0 = 32 - lane;  // d >= d0: columns right of the block
+        const CT *zb = y + i;
+        int d = c0 + 1;  // slices cover d in [1, W]
+        const int d1 = c1 + 1;
+        for (; d + 1 < d1; d += 2) {
+          a0 += (d >= d0) ? to_ct(row[d]) * zb[d] : CT(0);
+          a1 += (d + 1 >= d0) ? to_ct(row[d + 1]) * zb[d + 1] : CT(0);
+        }
+        if (d < d1) a0 += (d >= d0) ? to_ct(row[d]) * zb[d] : CT(0);
+      }
+      part[warp * 32 + lane] = a0 + a1;
+      if (__syncthreads_or(!ok)) {
+        // bounded drain of the copies still in flight, then give up
+        if (tid == 0)
+          for (int j = s; j < nb && j < s + NS; ++j) {
+            const uint32_t g2 = gcount + j;
+            mbar_wait(&mbar[g2 % NS], (g2 / NS) & 1u, timeout_ns);
+          }
+        __syncthreads();
+        gcount += nb < s + NS ? nb : s + NS;
+        return false;
+      }
+      if (warp == 0) {
+        CT c = y[i];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) c -= part[w * 32 + lane];
+        cbuf[lane] = c;
+        __syncwarp();
+        CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
+        if (dir == 0) {
+          const T *rb = row + W - lane;  // rb[m] = Linv[lane][m], m <= lane
+#pragma unroll
+          for (int m = 0; m < 32; m += 4) {
+            b0 += (m <= lane) ? to_ct(rb[m]) * cbuf[m] : CT(0);
+            b1 += (m + 1 <= lane) ? to_ct(rb[m + 1]) * cbuf[m + 1] : CT(0);
+            b2 += (m + 2 <= lane) ? to_ct(rb[m + 2]) * cbuf[m + 2] : CT(0);
+            b3 += (m + 3 <= lane) ? to_ct(rb[m + 3]) * cbuf[m + 3] : CT(0);
+          }
+        } else {
+#pragma unroll
+          for (int d = 0; d < 32; d += 4) {
+            b0 += (d < 32 - lane) ? to_ct(row[d]) * cbuf[lane + d] : CT(0);
+            b1 += (d + 1 < 32 - lane) ? to_ct(row[d + 1]) * cbuf[lane + d + 1] : CT(0);
+            b2 += (d + 2 < 32 - lane) ? to_ct(row[d + 2]) * cbuf[lane + d + 2] : CT(0);
+            b3 += (d + 3 < 32 - lane) ? to_ct(row[d + 3]) * cbuf[lane + d + 3] : CT(0);
+          }
+        }
+        y[i] = (b0 + b1) + (b2 + b3);
+      }
+      __syncthreads();
+      // every thread is done with stage st: refill it
+      if (tid == 0 && s + NS < nb) {
+        const int Kb = dir == 0 ? s + NS : nb - 1 - (s + NS);
+        fence_proxy_async();
+        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
+      }
+    }
+    gcount += nb;
+  }
+  return true;
 }
 
 // Banded Cholesky solve L L^T delta = r by warp 0. y[OFF + i] holds r on entry
@@ -733,11 +879,13 @@ __device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad,
 // m steps of textbook CG with A_p staged in shared memory (FP32 values,
 // int16 local columns) and the vectors r, d, q in registers: thread t owns
 // rows t, t + NT, t + 2 NT, ... Only p lives in shared memory. On entry p
-// holds r (zero beyond n); on exit it holds d.
-template <int NT, int RMAX>
+// holds r (zero beyond n); on exit it holds d. KC > 0 is the ELL width known
+// at compile time (KC = 0: runtime K). red holds 2 * NT/32 floats.
+template <int NT, int RMAX, int KC>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
                                 int m, float *p, float *red) {
   const int tid = threadIdx.x;
+  float *red0 = red, *red1 = red + NT / 32;
   float r[RMAX], d[RMAX], q[RMAX];
   float rr = 0.f;
 #pragma unroll
@@ -748,7 +896,8 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     q[k] = 0.f;
     rr += r[k] * r[k];
   }
-  rr = block_sum<NT, float>(rr, red);
+  __syncthreads();  // red buffers free
+  rr = block_sum_1b<NT, float>(rr, red0);
   for (int it = 0; it < m && rr != 0.f; ++it) {
     float pq = 0.f;
 #pragma unroll
@@ -756,14 +905,17 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
       const int i = tid + k * NT;
       if (i < n) {
         float s = 0.f;
+        if constexpr (KC > 0) {
 #pragma unroll
-        for (int e = 0; e < kMaxEll; ++e)
-          if (e < K) s += sval[e * npad + i] * p[scol[e * npad + i]];
+          for (int e = 0; e < KC; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+        } else {
+          for (int e = 0; e < K; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+        }
         q[k] = s;
         pq += p[i] * s;
       }
     }
-    pq = block_sum<NT, float>(pq, red);
+    pq = block_sum_1b<NT, float>(pq, red1);
     const float alpha = rr / pq;
     float rn = 0.f;
 #pragma unroll
@@ -775,7 +927,7 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
         rn += r[k] * r[k];
       }
     }
-    rn = block_sum<NT, float>(rn, red);
+    rn = block_sum_1b<NT, float>(rn, red0);
     const float beta = rn / rr;
     rr = rn;
 #pragma unroll
@@ -881,11 +1033,63 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
   }
 }
 
+// r_p = b[Omega_p] - A[Omega_p, :] x for the rows of one subdomain (thread t:
+// rows t, t + NT, ...), written to rhs in the compute type; accumulates
+// ||r||^2 over Omega_p and over its owned rows. KC > 0: ELL width at compile
+// time, so every column / value / x load of a row issues before the FMAs.
+template <int KC, typename CT, int NT>
+__device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, int K,
+                                            const double *xcur, bool async, CT *rhs,
+                                            double &a_loc, double &a_own) {
+  const int64_t eb = D.row_off * K;
+  for (int i = threadIdx.x; i < D.npad; i += NT) {
+    double r = 0.0;
+    if (i < D.n) {
+      const int g = S.gidx[D.row_off + i];
+      r = S.b[g];
+      if constexpr (KC > 0) {
+        int cols[KC];
+        double vals[KC], xs[KC];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          const int64_t e = eb + (int64_t)k * D.npad + i;
+          cols[k] = S.rcol[e];
+          vals[k] = S.rval[e];
+        }
+#pragma unroll
+        for (int k = 0; k < KC; ++k)
+          xs[k] = async ? ld_relaxed_f64(xcur + cols[k]) : __ldcg(xcur + cols[k]);
+#pragma unroll
+        for (int k = 0; k < KC; ++k) r -= vals[k] * xs[k];
+        if (S.ownf[D.row_off + i]) {
+          double xd = 0.0;
+#pragma unroll
+          for (int k = 0; k < KC; ++k) xd = cols[k] == g ? xs[k] : xd;
+          S.xg[D.row_off + i] = xd;
+        }
+      } else {
+        double xd = 0.0;
+        for (int k = 0; k < K; ++k) {
+          const int64_t e = eb + (int64_t)k * D.npad + i;
+          const int c = S.rcol[e];
+          const double xv = async ? ld_relaxed_f64(xcur + c) : __ldcg(xcur + c);
+          r -= S.rval[e] * xv;
+          xd = c == g ? xv : xd;
+        }
+        if (S.ownf[D.row_off + i]) S.xg[D.row_off + i] = xd;
+      }
+      a_loc += r * r;
+      if (S.ownf[D.row_off + i]) a_own += r * r;
+    }
+    rhs[i] = (CT)r;
+  }
+}
+
 // --------------------------------------------------------------------------
 // the persistent RAS kernel
 // --------------------------------------------------------------------------
 
-constexpr int kBandStages = 4;
+constexpr int kBandStages = 8;  // ring capacity; Launch::nstages of them are used
 constexpr int kYPad = 48;  // zero tail of y beyond W (vector overrun of the last chunk)
 
 template <int KIND, typename T, int NT>
@@ -900,11 +1104,11 @@ struct Smem {
     return ((size_t)(2 * Wmax + npad_max + kYPad) + 31) / 32 * 32;
   }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
-  static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax) {
+  static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax, int nstages) {
     if (KIND == kBand) {
-      size_t b = kBandStages * ring_stride(Wmax) * sizeof(T);
+      size_t b = (size_t)nstages * ring_stride(Wmax) * sizeof(T);
       b += ylen(Wmax, npad_max) * sizeof(CT);
-      b += 64 * sizeof(CT);
+      b += (64 + NT) * sizeof(CT);  // cbuf, per-warp partials
       return b;
     }
     if (KIND == kCGS) {
@@ -917,15 +1121,20 @@ struct Smem {
   }
 };
 
+// Resident CTAs per SM the register allocation is sized for: the 512-thread
+// variants (staged CG: ~175 KB of shared memory) run one CTA per SM, the
+// 256-thread variants two.
+template <int NT> struct MinBlocks { static constexpr int value = NT >= 512 ? 1 : 2; };
+
 template <int KIND, typename T, int NT>
-__global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Launch L) {
   using CT = typename CTypeOf<T>::type;
   using SM = Smem<KIND, T, NT>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ SysDesc s_sys;
   __shared__ SubDesc s_sub;
   __shared__ double s_red[NT / 32 * 2];
-  __shared__ CT s_redc[NT / 32];
+  __shared__ __align__(16) CT s_redc[2 * (NT / 32)];
   __shared__ int s_flag[8];
   __shared__ __align__(8) uint64_t s_mbar[kBandStages];
   __shared__ int s_done[kMaxCtaSys];
@@ -946,7 +1155,7 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
   if (KIND == kBand) {
     ring_stride = (int)SM::ring_stride(L.Wmax);
     ring = reinterpret_cast<T *>(smem);
-    ybuf = reinterpret_cast<CT *>(smem + kBandStages * ring_stride * sizeof(T));
+    ybuf = reinterpret_cast<CT *>(smem + (size_t)L.nstages * ring_stride * sizeof(T));
     cbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
@@ -961,9 +1170,11 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     v4 = KIND == kILU ? base + 4 * vl : nullptr;
   }
   uint32_t gcount = 0;
+  if (KIND == kBand)
+    for (int e = tid; e < 64; e += NT) cbuf[e] = CT(0);  // cbuf[32, 64) stays zero
   if (KIND == kBand || KIND == kCGS) {
     if (tid == 0) {
-      for (int s = 0; s < kBandStages; ++s) mbar_init(&s_mbar[s], 1);
+      for (int s = 0; s < L.nstages; ++s) mbar_init(&s_mbar[s], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
@@ -987,8 +1198,9 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     const SysDesc &S = s_sys;
     const SubDesc &D = s_sub;
     const int K = S.K;
-    const int64_t eb = D.row_off * K;
     CT *rhs = KIND == kBand ? ybuf + OFF : v0;
+    uint64_t t0 = 0, t1 = 0, t2 = 0;
+    if (tid == 0) t0 = gtimer();
     if (KIND == kCGS && tid == 0) {
       // stage A_p (values, columns) while the residual is gathered
       const size_t vl = SM::vec_len(L.npad_max);
@@ -1006,55 +1218,27 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
       for (int e = tid; e < L.Wmax + kYPad; e += NT) ybuf[OFF + D.npad + e] = CT(0);
     }
     double a_loc = 0.0, a_own = 0.0;
-    for (int i = tid; i < D.npad; i += NT) {
-      double r = 0.0;
-      if (i < D.n) {
-        r = S.b[S.gidx[D.row_off + i]];
-        // issue every column / value / x load of the row before the arithmetic
-        int cols[kMaxEll];
-        double vals[kMaxEll], xs[kMaxEll];
-#pragma unroll
-        for (int k = 0; k < kMaxEll; ++k)
-          if (k < K) {
-            const int64_t e = eb + (int64_t)k * D.npad + i;
-            cols[k] = S.rcol[e];
-            vals[k] = S.rval[e];
-          }
-#pragma unroll
-        for (int k = 0; k < kMaxEll; ++k)
-          if (k < K) xs[k] = async ? ld_relaxed_f64(xcur + cols[k]) : __ldcg(xcur + cols[k]);
-#pragma unroll
-        for (int k = 0; k < kMaxEll; ++k)
-          if (k < K) r -= vals[k] * xs[k];
-        for (int k = kMaxEll; k < K; ++k) {
-          const int64_t e = eb + (int64_t)k * D.npad + i;
-          const double xv = async ? ld_relaxed_f64(xcur + S.rcol[e]) : __ldcg(xcur + S.rcol[e]);
-          r -= S.rval[e] * xv;
-        }
-        a_loc += r * r;
-        if (S.ownf[D.row_off + i]) a_own += r * r;
-      }
-      rhs[i] = (CT)r;
-    }
+    if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+    else if (K == 7) gather_rows<7, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+    else gather_rows<0, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
     block_sum2<NT>(a_loc, a_own, s_red);
     res_loc = a_loc;
     res_own = a_own;
+    if (tid == 0) t1 = gtimer();
     // local solve
     CT *delta = rhs;
     if (KIND == kBand) {
-      bool ok = true;
-      if (tid < 32) {
-        const T *fac = reinterpret_cast<const T *>(S.fac);
-        const int64_t slab = (int64_t)32 * slab_stride(D.W, (int)sizeof(T));
-        const int nb = D.npad / 32;
-        ok = band_solve_warp<T, CT, kBandStages>(fac + D.fac_off, fac + D.fac_off + nb * slab, nb,
-                                                 D.W, ybuf, OFF, cbuf, ring, ring_stride, s_mbar,
-                                                 gcount, L.timeout_ns);
-        if (!ok && tid == 0) set_error(L.ctl, kETIMEOUT, 2);
-        if (tid == 0) s_flag[4] = ok ? 1 : 0;
-      }
       __syncthreads();
-      if (!s_flag[4]) return false;
+      const T *fac = reinterpret_cast<const T *>(S.fac);
+      const int64_t slab = (int64_t)32 * slab_stride(D.W, (int)sizeof(T));
+      const int nb = D.npad / 32;
+      const bool ok = band_solve_cta<T, CT, NT>(
+          fac + D.fac_off, fac + D.fac_off + nb * slab, nb, D.W, ybuf + OFF, cbuf, cbuf + 64, ring,
+          ring_stride, s_mbar, gcount, L.timeout_ns, L.nstages);
+      if (!ok) {
+        if (tid == 0) set_error(L.ctl, kETIMEOUT, 2);
+        return false;
+      }
     } else if (KIND == kCGS) {
       if (tid == 0) {
         const bool ok = mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);
@@ -1068,9 +1252,14 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
       __syncthreads();
       if (!s_flag[4]) return false;
       const size_t vl = SM::vec_len(L.npad_max);
-      cg_solve_staged<NT, (kStagedRows + NT - 1) / NT>(
-          reinterpret_cast<const float *>(smem), reinterpret_cast<const int16_t *>(smem + (size_t)L.kmax * vl * 4),
-          K, D.n, D.npad, L.m, reinterpret_cast<float *>(v0), reinterpret_cast<float *>(s_redc));
+      const float *sv = reinterpret_cast<const float *>(smem);
+      const int16_t *sc = reinterpret_cast<const int16_t *>(smem + (size_t)L.kmax * vl * 4);
+      float *pv = reinterpret_cast<float *>(v0);
+      float *rd = reinterpret_cast<float *>(s_redc);
+      constexpr int RM = (kStagedRows + NT - 1) / NT;
+      if (K == 5) cg_solve_staged<NT, RM, 5>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else if (K == 7) cg_solve_staged<NT, RM, 7>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else cg_solve_staged<NT, RM, 0>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
       delta = v0;
     } else if (KIND == kCG) {
       const int32_t *lc = S.lcol + D.row_off * K;
@@ -1083,18 +1272,27 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
       pcg_solve<T, CT, NT>(S, D, L.m, v0, v1, v2, v3, v4, s_redc);
       delta = v4;
     }
+    if (tid == 0) t2 = gtimer();
     // restricted prolongation: only owned rows are written (RAS)
     const int32_t *own = S.own_l + D.own_off;
     for (int t = tid; t < D.n_own; t += NT) {
       const int i = own[t];
       const int g = S.gidx[D.row_off + i];
-      if (async) {
-        st_relaxed_f64(xnext + g, ld_relaxed_f64(xcur + g) + (double)delta[i]);
-      } else {
-        __stcg(xnext + g, __ldcg(xcur + g) + (double)delta[i]);
-      }
+      // x_g + delta on an owned row is the owned part of the local solution
+      // computed from the very values this gather read, whatever other
+      // subdomains (or delays) did to x meanwhile
+      const double xn = S.xg[D.row_off + i] + (double)delta[i];
+      if (async) st_relaxed_f64(xnext + g, xn);
+      else __stcg(xnext + g, xn);
     }
+    __threadfence();
     __syncthreads();
+    if (tid == 0) {
+      SubState &ph = S.sub[s_flag[5]];
+      ph.t_gather += t1 - t0;
+      ph.t_solve += t2 - t1;
+      ph.t_update += gtimer() - t2;
+    }
     return true;
   };
 
@@ -1174,6 +1372,13 @@ __global__ void __launch_bounds__(NT) ras_main_kernel(Launch L) {
     }
   } else {
     // ----------------------------------------------------------- ASYNC
+    // per-launch update budget starts from zero (this CTA's own subdomains)
+    if (tid == 0)
+      for (int it = i0; it < i1; ++it) {
+        const Item item = L.items[it];
+        L.sys[item.sys].sub[item.p].step_updates = 0;
+      }
+    __syncthreads();
     uint64_t t_idle = gtimer();
     for (;;) {
       int any_work = 0, all_done = 1;
@@ -1366,9 +1571,9 @@ static int occupancy_t(size_t smem) {
     }                                                                                      \
   } while (0)
 
-size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax) {
+size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax, int nstages) {
   size_t r = 0;
-#define RAS_SMEM(K_, T_, NT_) r = Smem<K_, T_, NT_>::bytes(Wmax, npad_max, kmax)
+#define RAS_SMEM(K_, T_, NT_) r = Smem<K_, T_, NT_>::bytes(Wmax, npad_max, kmax, nstages)
   RAS_DISPATCH(kind, prec, nt, RAS_SMEM);
 #undef RAS_SMEM
   return r;

@@ -33,7 +33,7 @@ __host__ __device__ inline int slab_stride(int W, int esize) {
   return s;
 }
 
-size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax);
+size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax, int nstages);
 int main_threads(int kind, int nt_pref);
 int main_occupancy(int kind, int prec, int nt, size_t smem);
 cudaError_t launch_main(int kind, int prec, int nt, const Launch &L, int grid, size_t smem,

@@ -158,6 +158,20 @@ def test_async_converges_to_oracle_solution(kind, prec):
     ras.ras_destroy(ctx)
 
 
+def test_async_one_subdomain_per_cta_large_overlap():
+    # 64 subdomains with overlap 4, each CTA re-gathering its own subdomain
+    # right after updating it: the owned rows it re-reads must be the values it
+    # just wrote, or the correction is applied twice and the iteration diverges
+    N = 512
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 1)
+    part = ras.ras_partition_regular2d(N, N, 8, 8)
+    for prec in (F32, F64):
+        x, info = gpu_solve(A, b, part, 64, 4, BAND, prec, mode=ras.RAS_ASYNC, tol=1e-8)
+        assert info.status == 0, info.as_dict()
+        assert true_relres(A, b, x) < 1e-8
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_single_subdomain_one_iteration():
