@@ -178,11 +178,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline model
 
-def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m):
+def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
     """Algorithmic bytes of one local update of each subdomain:
     residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p,
-    local CG = nnz(A_p) (s_v + 2) m (matrix re-read every step),
-    band = 2 n_p (w_p + 1) s_f, update = 8 |O_p| written."""
+    local CG = nnz(A_p) (s_v + 2), once when A_p is staged in shared memory,
+    m times when it is re-read every step; band = 2 n_p (w_p + 1) s_f;
+    update = 8 |O_p| written."""
     rp, ci = A.row_ptr, A.col
     rownnz = np.diff(rp)
     out = []
@@ -198,7 +199,7 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m):
         nnz_p = int(inside[ci[idx]].sum())
         res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
         if kind == ras.RAS_LOCAL_CG:
-            loc = nnz_p * (prec_bytes + 2) * m
+            loc = nnz_p * (prec_bytes + 2) * (1 if staged else m)
         else:
             loc = 0
         out.append(res + loc + 8 * o_p)
@@ -337,7 +338,9 @@ def run_ours(args):
     # roofline of the persistent kernel
     info = infos[len(infos) // 2]
     counts = ras.ras_get_update_counts(ctxs[head_prec])
-    per_upd = subdomain_bytes(A, ras, ctxs[head_prec], ras.RAS_LOCAL_CG, 4, M_INNER)
+    launch = ras.ras_get_launch(ctxs[head_prec])
+    staged = launch["kernel_variant"] == 3
+    per_upd = subdomain_bytes(A, ras, ctxs[head_prec], ras.RAS_LOCAL_CG, 4, M_INNER, staged)
     alg_bytes = float(np.dot(counts, per_upd))
     kernel_s = info.kernel_ms / 1e3
     achieved = alg_bytes / kernel_s / 1e9
@@ -345,7 +348,9 @@ def run_ours(args):
     tpu = profile_traffic("async_fp32")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": (tpu * float(counts.sum())) if tpu else None,
-            "kernel": "ras_main_kernel<CG, float, 256>", "kernel_ms": info.kernel_ms,
+            "kernel": ("ras_main_kernel<CG staged in shared memory, float, %d>" if staged else
+                       "ras_main_kernel<CG, float, %d>") % launch["cta_threads"],
+            "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 
     launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)

@@ -162,14 +162,17 @@ typedef struct {
 } ras_tune_result;
 
 /* Launch-shape autotuner (not in the paper: the GPU counterpart of choosing
- * the local solver's parameters). Times `iters` updates of the real system
- * (b DEVICE; x_scratch DEVICE double[n], overwritten) for each candidate - CTA
- * threads 256 / 512 for CG and ILU-PCG, the shared-memory staged FP32 CG, and
- * with tune_inner != 0 the inner step counts m/2, m, 2m - and keeps the one
- * with the largest residual reduction per millisecond of kernel time. The
- * context then uses it for every solve. out may be NULL. */
-ras_status ras_autotune(ras_ctx *ctx, const double *b, double *x_scratch, int32_t mode,
-                        int32_t iters, int32_t tune_inner, ras_tune_result *out);
+ * the local solver's parameters). For each candidate - CTA threads 256 / 512
+ * for CG and ILU-PCG, the shared-memory staged FP32 CG, and with
+ * tune_inner != 0 the inner step counts m/2, m, 2m - it runs the context's
+ * system with a zero right-hand side from x = 1 (x_scratch: DEVICE double[n],
+ * overwritten), `iters` updates and then `iters` more. With b = 0 the error is
+ * x itself, dominated by the smoothest modes, so the second window's residual
+ * reduction per millisecond of kernel time is the asymptotic rate that sets
+ * time-to-solution. The best candidate is kept for every later solve. out may
+ * be NULL. */
+ras_status ras_autotune(ras_ctx *ctx, double *x_scratch, int32_t mode, int32_t iters,
+                        int32_t tune_inner, ras_tune_result *out);
 
 /* ------------------------------------------------------------------------ */
 /* Continuous batching (serving)                                             */
@@ -218,6 +221,13 @@ ras_status ras_get_info(const ras_ctx *ctx, int32_t *num_parts, int32_t *n, int3
 
 /* Per-subdomain local-update counts of the last solve: counts[num_parts]. */
 ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
+
+/* Launch shape the context uses: kernel_variant 0 banded Cholesky, 1 CG
+ * reading A_p from global memory, 2 ILU(0)-PCG, 3 CG with A_p staged in
+ * shared memory; threads per CTA; CTAs (one cooperative launch); CG / PCG
+ * steps per local solve. Any pointer may be NULL. */
+ras_status ras_get_launch(const ras_ctx *ctx, int32_t *kernel_variant, int32_t *cta_threads,
+                          int32_t *grid, int32_t *inner_iters);
 
 /* Runtime breakdown of the last solve, per subdomain (the per-update timing
  * of Sec. 4's Figs. 3a-7a): ns[3*p+0] nanoseconds spent gathering the local

@@ -96,7 +96,9 @@ def load():
             "ras_relres_noalloc": ([I32, P, P, P, P, P, P, P], C.c_int),
             "ras_solve_begin": ([P, P, P, D], C.c_int),
             "ras_get_phase_times": ([P, P], C.c_int),
-            "ras_autotune": ([P, P, P, I32, I32, I32, C.POINTER(ras_tune_result)], C.c_int),
+            "ras_get_launch": ([P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)],
+                               C.c_int),
+            "ras_autotune": ([P, P, I32, I32, I32, C.POINTER(ras_tune_result)], C.c_int),
             "ras_batch_step": ([P, I32, I32, I64, I64, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -233,12 +235,12 @@ def ras_solve_batch(ctxs, bs, xs, tol: float = 1e-8, mode: int = RAS_SYNC, max_u
     return list(infos)
 
 
-def ras_autotune(ctx: RasContext, b, x_scratch, mode: int = RAS_SYNC, iters: int = 20,
+def ras_autotune(ctx: RasContext, x_scratch, mode: int = RAS_SYNC, iters: int = 20,
                  tune_inner: bool = True) -> ras_tune_result:
     """Times candidate launch shapes / inner step counts and keeps the best."""
     out = ras_tune_result()
-    _check(load().ras_autotune(ctx.ptr, _dptr(b, ctx.n, "b"), _dptr(x_scratch, ctx.n, "x"), mode,
-                               iters, 1 if tune_inner else 0, C.byref(out)), "ras_autotune")
+    _check(load().ras_autotune(ctx.ptr, _dptr(x_scratch, ctx.n, "x"), mode, iters,
+                               1 if tune_inner else 0, C.byref(out)), "ras_autotune")
     return out
 
 
@@ -292,6 +294,14 @@ def ras_get_update_counts(ctx: RasContext) -> np.ndarray:
     out = np.zeros(ctx.num_parts, dtype=np.int64)
     _check(load().ras_get_update_counts(ctx.ptr, out.ctypes.data), "ras_get_update_counts")
     return out
+
+
+def ras_get_launch(ctx: RasContext) -> dict:
+    v, t, g, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().ras_get_launch(ctx.ptr, C.byref(v), C.byref(t), C.byref(g), C.byref(m)),
+           "ras_get_launch")
+    return {"kernel_variant": v.value, "cta_threads": t.value, "grid": g.value,
+            "inner_iters": m.value}
 
 
 def ras_get_phase_times(ctx: RasContext) -> np.ndarray:

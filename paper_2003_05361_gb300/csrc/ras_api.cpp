@@ -687,7 +687,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     d.n = (int32_t)mp.omega.size();
     d.npad = (d.n + 31) / 32 * 32;
     d.n_own = (int32_t)owned_lists[p].size();
-    d.W = std::max(mp.w, 31);
+    d.W = std::max(mp.w, 1);
     d.row_off = rows;
     d.own_off = owns;
     d.fac_off = fac;
@@ -698,7 +698,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     nbrs += d.n_nbr;
     if (kind == RAS_LOCAL_BANDCHOL) {
       if (mp.w > 160) return RAS_ENOTSUP;
-      fac += 2ll * (d.npad / 32) * 32 * slab_stride(d.W, (int)prec_bytes(prec));
+      fac += 2ll * (d.npad / 32) * 32 * d.W + (int64_t)(d.npad / 32) * 528;
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
@@ -977,6 +977,7 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.persist = 1;
   L.kmax = pl.kmax;
   L.nstages = pl.nstages;
+  L.band_direct = (int32_t)env_int("RAS_BAND_DIRECT", 0);
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   const int nitems = (int)pl.items.size();
@@ -1169,6 +1170,11 @@ namespace {
 // reused while the same contexts, in the same order, are stepped.
 struct StepCache {
   std::vector<uint64_t> key;  // serials of the stepped contexts, in order
+  int32_t mode = -1;
+  int64_t step_limit = -1, max_updates = -1;
+  cudaGraphExec_t graph = nullptr;  // captured step sequence (null: launch directly)
+  bool graph_failed = false;
+  cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
   LaunchPlan plan;
   SysDesc *d_sys = nullptr;
   GridCtl *d_ctl = nullptr;
@@ -1177,6 +1183,11 @@ struct StepCache {
   SysState *h_st = nullptr;  // pinned
   int cap = 0;
   void release() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    graph_failed = false;
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
     plan.release();
     cudaFree(d_sys);
     cudaFree(d_ctl);
@@ -1251,8 +1262,6 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
     if (!ctxs[s]->finished) ++running;
     if (ctxs[s]->stream != stream) CUDA_TRY(cudaStreamWaitEvent(stream, ctxs[s]->ev_begin, 0));
   }
-  CUDA_TRY(cudaMemcpyAsync(sc.d_sys, sc.h_sys, sizeof(SysDesc) * num, cudaMemcpyHostToDevice,
-                           stream));
   Launch L{};
   L.sys = sc.d_sys;
   L.nsys = num;
@@ -1273,18 +1282,58 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   L.persist = 0;
   L.kmax = sc.plan.kmax;
   L.nstages = sc.plan.nstages;
+  L.band_direct = (int32_t)env_int("RAS_BAND_DIRECT", 0);
   std::memset(sc.h_ctl, 0, sizeof(GridCtl));
   sc.h_ctl->remaining = running;
   const int nitems = (int)sc.plan.items.size();
-  CUDA_TRY(cudaMemcpyAsync(sc.d_ctl, sc.h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(launch_main(c0->exec_kind, c0->ls.prec, sc.plan.nt, L, sc.plan.grid, sc.plan.smem,
-                       stream));
-  if (mode == RAS_SYNC) CUDA_TRY(launch_copyback(L, nitems, stream));
-  CUDA_TRY(launch_residual(L, nitems, stream));
-  for (int s = 0; s < num; ++s)
-    CUDA_TRY(cudaMemcpyAsync(&sc.h_st[s], ctxs[s]->d_st, sizeof(SysState), cudaMemcpyDeviceToHost,
-                             stream));
-  CUDA_TRY(cudaMemcpyAsync(sc.h_ctl, sc.d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, stream));
+  // The whole step: descriptors in (from pinned staging, read at execution
+  // time), the persistent launch, copy-back, residual, state out.
+  auto issue = [&](cudaStream_t sm) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(sc.d_sys, sc.h_sys, sizeof(SysDesc) * num,
+                                    cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sc.d_ctl, sc.h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess)
+      e = launch_main(c0->exec_kind, c0->ls.prec, sc.plan.nt, L, sc.plan.grid, sc.plan.smem, sm);
+    if (e == cudaSuccess && mode == RAS_SYNC) e = launch_copyback(L, nitems, sm);
+    if (e == cudaSuccess) e = launch_residual(L, nitems, sm);
+    for (int s = 0; s < num && e == cudaSuccess; ++s)
+      e = cudaMemcpyAsync(&sc.h_st[s], ctxs[s]->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, sm);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(sc.h_ctl, sc.d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, sm);
+    return e;
+  };
+  if (sc.mode != mode || sc.step_limit != step_limit || sc.max_updates != max_updates) {
+    if (sc.graph) cudaGraphExecDestroy(sc.graph);
+    sc.graph = nullptr;
+    sc.graph_failed = false;
+    sc.mode = mode;
+    sc.step_limit = step_limit;
+    sc.max_updates = max_updates;
+  }
+  const bool use_graph = env_int("RAS_STEP_GRAPH", 1) != 0;
+  if (use_graph && !sc.graph && !sc.graph_failed) {
+    // captured on a private stream, so work other host threads put on the
+    // caller's stream meanwhile is never swept into the graph
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = sc.cap_stream ? cudaSuccess
+                                  : cudaStreamCreateWithFlags(&sc.cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(sc.cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t ei = issue(sc.cap_stream);
+      e = cudaStreamEndCapture(sc.cap_stream, &gr);
+      if (ei != cudaSuccess) e = ei;
+    }
+    if (e == cudaSuccess && gr) e = cudaGraphInstantiate(&sc.graph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      sc.graph = nullptr;
+      sc.graph_failed = true;  // capture refused: launch directly from now on
+      cudaGetLastError();
+    }
+  }
+  if (sc.graph) CUDA_TRY(cudaGraphLaunch(sc.graph, stream));
+  else CUDA_TRY(issue(stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
   ras_status first = sc.h_ctl->status != 0 ? (ras_status)sc.h_ctl->status : RAS_OK;
   std::vector<int> newly;
@@ -1311,10 +1360,18 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   return first;
 }
 
-ras_status ras_autotune(ras_ctx *c, const double *b, double *x_scratch, int32_t mode,
-                        int32_t iters, int32_t tune_inner, ras_tune_result *out) {
-  if (!c || !b || !x_scratch || iters <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
+ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t iters,
+                        int32_t tune_inner, ras_tune_result *out) {
+  if (!c || !x_scratch || iters <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
     return RAS_EINVAL;
+  // homogeneous problem A x = 0 from x = 1: the error is x itself, dominated
+  // by the smoothest modes, so a short window sees the asymptotic rate
+  if (!c->d_bx) {
+    ras_status s = c->alloc(c->d_bx, 2 * (size_t)c->n);
+    if (s != RAS_OK) return s;
+  }
+  double *b = c->d_bx;
+  CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * c->n, c->stream));
   struct Cand {
     int exec_kind, nt, m;
   };
@@ -1351,16 +1408,18 @@ ras_status ras_autotune(ras_ctx *c, const double *b, double *x_scratch, int32_t 
     const int ek = c->exec_kind;
     c->exec_kind = cd.exec_kind;
     c->ls.inner_iters = cd.m;
-    CUDA_TRY(cudaMemsetAsync(x_scratch, 0, sizeof(double) * c->n, c->stream));
-    ras_solve_info info{};
-    ras_status rs = ras_solve(c, b, x_scratch, 1e-300, mode, iters, &info);
+    // window 1 (transient), then window 2 from its result (timed): the score
+    // is the residual reduction per kernel millisecond of window 2
+    CUDA_TRY(launch_fill(x_scratch, 1.0, c->n, c->stream));
+    ras_solve_info info1{}, info{};
+    ras_status rs = ras_solve(c, b, x_scratch, 1e-300, mode, iters, &info1);
+    if (rs == RAS_OK || rs == RAS_ENOCONV) rs = ras_solve(c, b, x_scratch, 1e-300, mode, iters, &info);
     std::swap(pl, c->plan);
     c->exec_kind = ek;
     pl.release();
     if (rs != RAS_OK && rs != RAS_ENOCONV) continue;
     ++tried;
-    // residual reduction per millisecond (relres starts at 1 from x0 = 0)
-    const double red = -std::log(std::max(info.relres, 1e-300));
+    const double red = std::log(std::max(info1.relres, 1e-300) / std::max(info.relres, 1e-300));
     const double score = red / std::max(info.kernel_ms, 1e-6);
     if (score > best) {
       best = score;
@@ -1410,6 +1469,16 @@ ras_status ras_get_info(const ras_ctx *c, int32_t *num_parts, int32_t *n, int32_
 ras_status ras_get_update_counts(const ras_ctx *c, int64_t *counts) {
   if (!c || !counts) return RAS_EINVAL;
   std::copy(c->last_updates.begin(), c->last_updates.end(), counts);
+  return RAS_OK;
+}
+
+ras_status ras_get_launch(const ras_ctx *c, int32_t *kernel_variant, int32_t *cta_threads,
+                          int32_t *grid, int32_t *inner_iters) {
+  if (!c) return RAS_EINVAL;
+  if (kernel_variant) *kernel_variant = c->exec_kind;
+  if (cta_threads) *cta_threads = c->plan.nt;
+  if (grid) *grid = c->plan.grid;
+  if (inner_iters) *inner_iters = c->ls.inner_iters;
   return RAS_OK;
 }
 

@@ -32,10 +32,10 @@ struct SubDesc {
   int32_t n;        // |Omega_p|
   int32_t npad;     // n rounded up to a multiple of 32
   int32_t n_own;    // |O_p|
-  int32_t W;        // band: storage half-width (>= 31); slab = (W+1)*32 entries
+  int32_t W;        // band: half-bandwidth w (>= 1); slab = 32 * W entries
   int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
   int64_t own_off;  // offset into own_l
-  int64_t fac_off;  // band: first slab (entries); forward slabs then backward
+  int64_t fac_off;  // band: forward slabs, backward slabs, packed inverse blocks
   int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
   int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
   int32_t nlev_f;   // ILU: number of forward / backward levels
@@ -144,7 +144,7 @@ struct Launch {
   int32_t persist;             // async: keep polling until every system is done
   int32_t kmax;                // largest ELL width over the launch
   int32_t nstages;             // band: slab ring depth (2..8)
-  int32_t pad2_;
+  int32_t band_direct;         // band: 1 = warps read their slab slices from global memory
 };
 
 }  // namespace ras

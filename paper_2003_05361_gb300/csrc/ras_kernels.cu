@@ -320,23 +320,22 @@ __global__ void __launch_bounds__(256) band_chol_kernel(const BandJob *jobs, dou
 }
 
 // --------------------------------------------------------------------------
-// setup: slab layout for the blocked triangular solves
+// setup: operators of the blocked triangular solves
 // --------------------------------------------------------------------------
 //
-// Rows are grouped in blocks of 32. With W = storage half-width (>= 31 and
-// >= the true half-width w) and S = slab_stride(W), block K's FORWARD slab
-// holds for each lane l (row i = 32K + l) a contiguous row F[l][0..S):
-//   t <  W - l : L[i][i - W + t]            (columns left of the block)
-//   W-l <= t <= W : Linv_KK[l][t - (W - l)]  (row l of the inverse diagonal block)
-//   t >  W : 0
-// and its BACKWARD slab, for U = L^T, B[l][0..S):
-//   d <  32 - l : Uinv_KK[l][l + d] = Linv_KK[l + d][l]
-//   32-l <= d <= W : U[i][i + d] = L[i + d][i]   (columns right of the block)
-//   d >  W : 0
-// so the forward step of block K is  y_K = Linv_KK (r_K - L_{K,left} y_left)
-// and the backward step  z_K = Uinv_KK (y_K - U_{K,right} z_right); each row
-// reads its w+1 useful entries from one contiguous slab. Rows i >= n are
-// identity rows.
+// Rows are grouped in blocks of 32 (K = 0..nb-1; rows >= n are identity rows).
+// With L_KK the diagonal block of the Cholesky factor and W = the local
+// half-bandwidth w, forward substitution block by block is
+//   y_K = L_KK^{-1} (r_K - L_{K,left} y_left) = t_K - M_K y[32K-W, 32K),
+//   t_K = L_KK^{-1} r_K,  M_K = L_KK^{-1} L[K rows, 32K-W .. 32K)   (32 x W)
+// and backward substitution with U = L^T
+//   z_K = t'_K - M'_K z[32K+32, 32K+32+W),  t'_K = U_KK^{-1} y_K,
+//   M'_K = U_KK^{-1} U[K rows, 32K+32 .. 32K+32+W)                   (32 x W).
+// Per subdomain the storage is: nb forward slabs M_K, nb backward slabs M'_K
+// (each column-major, entry (l, c) at c*32 + l), then nb inverse diagonal
+// blocks L_KK^{-1} packed by diagonals (entry (l, l-e) at off(e) + l - e with
+// off(e) = 32e - e(e-1)/2, 528 entries per block); U_KK^{-1}[l][l+e] =
+// L_KK^{-1}[l+e][l] is read from the same storage at off(e) + l.
 template <typename T>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
@@ -344,11 +343,9 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
   __shared__ double X[32][33];
   const LayoutJob jb = jobs[blockIdx.x];
   const int l = threadIdx.x;
-  const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, ld = w + 1;
-  const int S = slab_stride(W, (int)sizeof(T));
+  const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, nb = jb.nb, ld = w + 1;
   const double *Bd = band + jb.band_off;
   const int i = 32 * K + l;
-  // diagonal block, row l
   for (int m = 0; m < 32; ++m) {
     double v = 0.0;
     const int jcol = 32 * K + m;
@@ -360,15 +357,15 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     Lkk[l][m] = v;
   }
   __syncwarp();
-  // lane m computes column m of the inverse by forward substitution
   {
+    // lane m computes column m of the inverse by forward substitution
     const int m = l;
     double col[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       double s = (r == m) ? 1.0 : 0.0;
       if (r >= m) {
-        for (int k = m; k < r; ++k) s -= Lkk[r][k] * col[k];
+        for (int q = m; q < r; ++q) s -= Lkk[r][q] * col[q];
         col[r] = s / Lkk[r][r];
       } else {
         col[r] = 0.0;
@@ -378,29 +375,32 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) X[r][m] = col[r];
   }
   __syncwarp();
-  const int64_t slab = (int64_t)32 * S;
-  T *F = fac + jb.fac_off + (int64_t)K * slab + (int64_t)l * S;
-  T *Bk = fac + jb.fac_off + (int64_t)jb.nb * slab + (int64_t)K * slab + (int64_t)l * S;
-  for (int t = 0; t < S; ++t) {
-    double v = 0.0;
-    if (t < W - l) {
-      const int jcol = i - W + t;
-      const int tb = t - W + w;  // index in the stored band row
-      v = (i < n && jcol >= 0 && tb >= 0) ? Bd[(int64_t)i * ld + tb] : 0.0;
-    } else if (t <= W) {
-      v = X[l][t - (W - l)];
-    }
-    F[t] = from_double<T>(v);
+  const int64_t slab = (int64_t)32 * W;
+  T *F = fac + jb.fac_off + (int64_t)K * slab;
+  T *Bk = fac + jb.fac_off + (int64_t)nb * slab + (int64_t)K * slab;
+  T *I = fac + jb.fac_off + 2 * (int64_t)nb * slab + (int64_t)K * 528;
+  for (int e = 0; e <= l; ++e) I[32 * e - e * (e - 1) / 2 + (l - e)] = from_double<T>(X[l][l - e]);
+  // M_K[l][c] = sum_{m <= l} Linv[l][m] L[32K+m][32K-W+c]
+  for (int c = 0; c < W; ++c) {
+    const int col = 32 * K - W + c;
+    double s = 0.0;
+    if (col >= 0)
+      for (int m = 0; m <= l; ++m) {
+        const int r = 32 * K + m;
+        if (r < n && col >= r - w) s += X[l][m] * Bd[(int64_t)r * ld + (col - r + w)];
+      }
+    F[(int64_t)c * 32 + l] = from_double<T>(s);
   }
-  for (int d = 0; d < S; ++d) {
-    double v = 0.0;
-    if (d < 32 - l) {
-      v = X[l + d][l];
-    } else if (d <= W) {
-      const int r = i + d;
-      v = (i < n && r < n && d <= w) ? Bd[(int64_t)r * ld + (w - d)] : 0.0;
-    }
-    Bk[d] = from_double<T>(v);
+  // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c],  U[a][b] = L[b][a]
+  for (int c = 0; c < W; ++c) {
+    const int r = 32 * K + 32 + c;
+    double s = 0.0;
+    if (r < n)
+      for (int m = l; m < 32; ++m) {
+        const int col = 32 * K + m;
+        if (col >= r - w) s += X[m][l] * Bd[(int64_t)r * ld + (col - r + w)];
+      }
+    Bk[(int64_t)c * 32 + l] = from_double<T>(s);
   }
 }
 
@@ -506,227 +506,108 @@ __global__ void __launch_bounds__(128) ras_copyback_kernel(Launch L) {
 // local solvers
 // --------------------------------------------------------------------------
 
-// 16-byte vector loads from shared memory, widened to the compute type.
-template <typename T> struct Vec16;
-template <> struct Vec16<float> {
-  static constexpr int V = 4;
-  __device__ __forceinline__ static void load(const float *p, float *o) {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-  }
-};
-template <> struct Vec16<double> {
-  static constexpr int V = 2;
-  __device__ __forceinline__ static void load(const double *p, double *o) {
-    const double2 v = *reinterpret_cast<const double2 *>(p);
-    o[0] = v.x; o[1] = v.y;
-  }
-};
-template <> struct Vec16<__nv_bfloat16> {
-  static constexpr int V = 8;
-  __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float *o) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(p);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      __nv_bfloat162 h;
-      memcpy(&h, &w[j], 4);
-      const float2 f = __bfloat1622float2(h);
-      o[2 * j] = f.x;
-      o[2 * j + 1] = f.y;
-    }
-  }
-};
+// Offset of diagonal e in a packed inverse diagonal block (528 entries).
+__device__ __forceinline__ int diag_off(int e) { return 32 * e - e * (e - 1) / 2; }
 
-// One forward block (lane l, row i = 32K + l): c = r_i - sum_{t < W-l} F[l][t] y[i-W+t],
-// then y_i = sum_{m <= l} Linv[l][m] c_m. `row` is this lane's slab row, y is
-// indexed so that y[0] is global row 0. Every shared load below is in bounds
-// and reads finite data (slab rows, zero-padded y, cbuf), so out-of-range
-// terms are removed with selects instead of predicated loads, which lets the
-// unrolled loops issue their loads ahead of the FMAs.
-template <typename T, typename CT>
-__device__ __forceinline__ void band_fwd_block(const T *row, CT *y, int i, int W, int lane,
-                                               CT *cbuf) {
-  using VL = Vec16<T>;
-  constexpr int V = VL::V;
-  const CT *yb = y + i - W;
-  CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
-  const int tfull = ((W - 31) / V) * V;  // t < tfull: every lane is off-block
-#pragma unroll 4
-  for (int t = 0; t < tfull; t += V) {
-    CT v[V];
-    VL::load(row + t, v);
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const CT pr = v[u] * yb[t + u];
-      if ((u & 3) == 0) a0 -= pr;
-      else if ((u & 3) == 1) a1 -= pr;
-      else if ((u & 3) == 2) a2 -= pr;
-      else a3 -= pr;
-    }
-  }
-  const int lim = W - lane;
-#pragma unroll 4
-  for (int t = tfull; t < W; t += V) {
-    CT v[V];
-    VL::load(row + t, v);
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const CT pr = (t + u < lim) ? v[u] * yb[t + u] : CT(0);
-      if ((u & 3) == 0) a0 -= pr;
-      else if ((u & 3) == 1) a1 -= pr;
-      else if ((u & 3) == 2) a2 -= pr;
-      else a3 -= pr;
-    }
-  }
-  cbuf[lane] = (a0 + a1) + (a2 + a3);
-  __syncwarp();
-  const T *rb = row + W - lane;  // rb[m] = Linv[lane][m] for m <= lane
-  CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
-#pragma unroll
-  for (int m = 0; m < 32; m += 4) {
-    CT c4[4];
-    if constexpr (sizeof(CT) == 4) {
-      const float4 cv = *reinterpret_cast<const float4 *>(cbuf + m);
-      c4[0] = cv.x; c4[1] = cv.y; c4[2] = cv.z; c4[3] = cv.w;
-    } else {
-      const double2 c01 = *reinterpret_cast<const double2 *>(cbuf + m);
-      const double2 c23 = *reinterpret_cast<const double2 *>(cbuf + m + 2);
-      c4[0] = c01.x; c4[1] = c01.y; c4[2] = c23.x; c4[3] = c23.y;
-    }
-    b0 += (m <= lane) ? to_ct(rb[m]) * c4[0] : CT(0);
-    b1 += (m + 1 <= lane) ? to_ct(rb[m + 1]) * c4[1] : CT(0);
-    b2 += (m + 2 <= lane) ? to_ct(rb[m + 2]) * c4[2] : CT(0);
-    b3 += (m + 3 <= lane) ? to_ct(rb[m + 3]) * c4[3] : CT(0);
-  }
-  y[i] = (b0 + b1) + (b2 + b3);
-  __syncwarp();
-}
-
-// One backward block: c = y_i - sum_{32-l <= d <= W} B[l][d] z[i+d], then
-// z_i = sum_{d <= 31-l} Uinv[l][l+d] c_{l+d}. cbuf has 64 entries, the upper
-// 32 zero, so cbuf[l + d] is in bounds for every d < 32.
-template <typename T, typename CT>
-__device__ __forceinline__ void band_bwd_block(const T *row, CT *y, int i, int W, int lane,
-                                               CT *cbuf) {
-  using VL = Vec16<T>;
-  constexpr int V = VL::V;
-  const CT *zb = y + i;
-  CT a0 = y[i], a1 = CT(0), a2 = CT(0), a3 = CT(0);
-  const int d0 = 32 - lane;
-#pragma unroll
-  for (int d = 0; d < 32; d += V) {
-    CT v[V];
-    VL::load(row + d, v);
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const CT pr = (d + u >= d0 && d + u <= W) ? v[u] * zb[d + u] : CT(0);
-      if ((u & 3) == 0) a0 -= pr;
-      else if ((u & 3) == 1) a1 -= pr;
-      else if ((u & 3) == 2) a2 -= pr;
-      else a3 -= pr;
-    }
-  }
-  // d in [32, W]: entries of the last chunk beyond W are zero in the slab and
-  // z beyond the subdomain is zero
-#pragma unroll 4
-  for (int d = 32; d <= W; d += V) {
-    CT v[V];
-    VL::load(row + d, v);
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const CT pr = v[u] * zb[d + u];
-      if ((u & 3) == 0) a0 -= pr;
-      else if ((u & 3) == 1) a1 -= pr;
-      else if ((u & 3) == 2) a2 -= pr;
-      else a3 -= pr;
-    }
-  }
-  cbuf[lane] = (a0 + a1) + (a2 + a3);
-  __syncwarp();
-  CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
-#pragma unroll
-  for (int d = 0; d < 32; d += V) {
-    CT v[V];
-    VL::load(row + d, v);
-#pragma unroll
-    for (int u = 0; u < V; ++u) {
-      const CT pr = (d + u < 32 - lane) ? v[u] * cbuf[lane + d + u] : CT(0);
-      if ((u & 3) == 0) b0 += pr;
-      else if ((u & 3) == 1) b1 += pr;
-      else if ((u & 3) == 2) b2 += pr;
-      else b3 += pr;
-    }
-  }
-  y[i] = (b0 + b1) + (b2 + b3);
-  __syncwarp();
-}
-
-// Banded Cholesky solve L L^T delta = r by the whole CTA (NT threads, NW =
-// NT/32 warps). For each 32-row block the off-block dot products (the part
-// that reads earlier / later blocks) are split over the warps by column
-// slices; warp 0 adds the NW partials in a fixed order, applies the inverse
-// diagonal block and publishes the 32 new values; two CTA barriers per block.
-// y[i] (local row i) holds r on entry and delta on exit; y[-W, 0) and
-// y[npad, npad+W+16) must be zero. Slabs stream through an NS-stage ring with
-// bulk copies issued by thread 0, up to NS blocks ahead.
-template <typename T, typename CT, int NT>
-__device__ bool band_solve_cta(const T *slabF, const T *slabB, int nb, int W, CT *y, CT *cbuf,
-                               CT *part, T *ring, int ring_stride, uint64_t *mbar,
-                               uint32_t &gcount, int64_t timeout_ns, const int NS) {
+// t = blockdiag(L_KK^{-1}) v (fwd) or blockdiag(U_KK^{-1}) v (!fwd) for every
+// block, warps taking blocks round-robin; the inverse blocks are read straight
+// from global memory (coalesced along each diagonal), four blocks per warp in
+// flight.
+template <typename T, typename CT, int NT, bool FWD>
+__device__ __forceinline__ void band_diag_apply(const T *__restrict__ I, int nb, const CT *v,
+                                                CT *t) {
   constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int K0 = warp; K0 < nb; K0 += 4 * NW) {
+    CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int K = K0 + h * NW;
+        if (K < nb) {
+          if (FWD) {
+            if (e <= lane)
+              acc[h] += to_ct(I[(int64_t)K * 528 + diag_off(e) + lane - e]) * v[32 * K + lane - e];
+          } else {
+            if (e <= 31 - lane)
+              acc[h] += to_ct(I[(int64_t)K * 528 + diag_off(e) + lane]) * v[32 * K + lane + e];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int K = K0 + h * NW;
+      if (K < nb) t[32 * K + lane] = acc[h];
+    }
+  }
+}
+
+// Banded Cholesky solve L L^T delta = r by the whole CTA: t = blockdiag(Linv) r;
+// forward chain y_K = t_K - M_K y_window; t' = blockdiag(Uinv) y; backward
+// chain z_K = t'_K - M'_K z_window. In a chain step every warp takes a slice
+// of the W window columns (the window values, the last few finished blocks,
+// stay in registers and are broadcast by warp-uniform shuffles), writes its
+// 32 partial sums, and after ONE barrier every warp adds the partials in the
+// same fixed order, so all warps hold identical y_K. y[0..npad) holds r on
+// entry and delta on exit; t is an npad scratch vector; part holds
+// 2 * NT partials. The slabs M_K / M'_K stream through an NS-stage ring with
+// bulk copies issued by thread 0 (the ring is written only by the copies and
+// read only before the barrier that precedes each refill, so no proxy fence
+// is needed).
+template <typename T, typename CT, int NT>
+__device__ bool band_solve_m(const T *F, const T *Bs, const T *I, int nb, int W, CT *y, CT *t,
+                             CT *part, T *ring, int ring_stride, uint64_t *mbar, uint32_t &gcount,
+                             int64_t timeout_ns, const int NS, const bool direct) {
+  constexpr int NW = NT / 32;
+  constexpr int NREG = 6;  // finished blocks kept in registers (W <= 160)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = slab_stride(W, (int)sizeof(T));
-  const int64_t slab = (int64_t)32 * S;
+  const int64_t slab = (int64_t)32 * W;
   const uint32_t bytes = (uint32_t)(slab * sizeof(T));
-  const int tw = (W + NW - 1) / NW;  // columns per warp slice
+  const int tw = (W + NW - 1) / NW;
+  const int c0 = warp * tw;
+  const int c1 = c0 + tw < W ? c0 + tw : W;
   for (int dir = 0; dir < 2; ++dir) {
-    const T *base = dir == 0 ? slabF : slabB;
-    const int pro = nb < NS ? nb : NS;
-    if (tid == 0)
+    const T *base = dir == 0 ? F : Bs;
+    if (tid == 0 && !direct) {
+      const int pro = nb < NS ? nb : NS;
       for (int j = 0; j < pro; ++j) {
         const int Kb = dir == 0 ? j : nb - 1 - j;
-        const uint32_t st = (gcount + j) % NS;
-        fence_proxy_async();
-        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
+        tma_load_1d(ring + ((gcount + j) % NS) * ring_stride, base + Kb * slab, bytes,
+                    &mbar[(gcount + j) % NS]);
       }
+    }
+    if (dir == 0) band_diag_apply<T, CT, NT, true>(I, nb, y, t);
+    else band_diag_apply<T, CT, NT, false>(I, nb, y, t);
+    __syncthreads();
+    CT yr[NREG];
+#pragma unroll
+    for (int j = 0; j < NREG; ++j) yr[j] = CT(0);
     for (int s = 0; s < nb; ++s) {
       const uint32_t g = gcount + s;
       const uint32_t st = g % NS;
-      const bool ok = mbar_wait(&mbar[st], (g / NS) & 1u, timeout_ns);
-      const T *row = ring + st * ring_stride + lane * S;
+      const bool ok = direct ? true : mbar_wait(&mbar[st], (g / NS) & 1u, timeout_ns);
       const int K = dir == 0 ? s : nb - 1 - s;
-      const int i = 32 * K + lane;
-      // off-block partial of this warp's column slice
-      CT a0 = CT(0), a1 = CT(0);
-      const int c0 = warp * tw;
-      const int c1 = c0 + tw < W ? c0 + tw : W;
-      if (!ok) {
-        // slab never arrived: contribute nothing, fail at the barrier below
-      } else if (dir == 0) {
-        const int lim = W - lane;  // t < lim: columns left of the block
-        const CT *yb = y + i - W;
-        int t = c0;
-        for (; t + 1 < c1; t += 2) {
-          a0 += (t < lim) ? to_ct(row[t]) * yb[t] : CT(0);
-          a1 += (t + 1 < lim) ? to_ct(row[t + 1]) * yb[t + 1] : CT(0);
+      CT acc = CT(0);
+      if (ok) {
+        // slab of block K: from the ring, or straight from global memory
+        const T *sl = direct ? base + K * slab : ring + st * ring_stride;
+        for (int c = c0; c < c1; ++c) {
+          // window row of column c and its distance (in blocks) from block K
+          const int grow = dir == 0 ? 32 * K - W + c : 32 * K + 32 + c;
+          const int dist = dir == 0 ? K - (grow >> 5) : (grow >> 5) - K;  // >= 1
+          CT src = CT(0);
+#pragma unroll
+          for (int j = 0; j < NREG; ++j) src = (dist - 1 == j) ? yr[j] : src;
+          const CT yv = __shfl_sync(0xffffffffu, src, grow & 31);
+          acc += to_ct(sl[c * 32 + lane]) * yv;
         }
-        if (t < c1) a0 += (t < lim) ? to_ct(row[t]) * yb[t] : CT(0);
-      } else {
-        const int d0 = 32 - lane;  // d >= d0: columns right of the block
-        const CT *zb = y + i;
-        int d = c0 + 1;  // slices cover d in [1, W]
-        const int d1 = c1 + 1;
-        for (; d + 1 < d1; d += 2) {
-          a0 += (d >= d0) ? to_ct(row[d]) * zb[d] : CT(0);
-          a1 += (d + 1 >= d0) ? to_ct(row[d + 1]) * zb[d + 1] : CT(0);
-        }
-        if (d < d1) a0 += (d >= d0) ? to_ct(row[d]) * zb[d] : CT(0);
       }
-      part[warp * 32 + lane] = a0 + a1;
+      CT *pb = part + (s & 1) * NT;
+      pb[warp * 32 + lane] = acc;
       if (__syncthreads_or(!ok)) {
-        // bounded drain of the copies still in flight, then give up
-        if (tid == 0)
+        if (tid == 0 && !direct)
           for (int j = s; j < nb && j < s + NS; ++j) {
             const uint32_t g2 = gcount + j;
             mbar_wait(&mbar[g2 % NS], (g2 / NS) & 1u, timeout_ns);
@@ -735,106 +616,24 @@ __device__ bool band_solve_cta(const T *slabF, const T *slabB, int nb, int W, CT
         gcount += nb < s + NS ? nb : s + NS;
         return false;
       }
-      if (warp == 0) {
-        CT c = y[i];
+      // every warp forms the same y_K
+      CT v = t[32 * K + lane];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) c -= part[w * 32 + lane];
-        cbuf[lane] = c;
-        __syncwarp();
-        CT b0 = CT(0), b1 = CT(0), b2 = CT(0), b3 = CT(0);
-        if (dir == 0) {
-          const T *rb = row + W - lane;  // rb[m] = Linv[lane][m], m <= lane
+      for (int w = 0; w < NW; ++w) v -= pb[w * 32 + lane];
 #pragma unroll
-          for (int m = 0; m < 32; m += 4) {
-            b0 += (m <= lane) ? to_ct(rb[m]) * cbuf[m] : CT(0);
-            b1 += (m + 1 <= lane) ? to_ct(rb[m + 1]) * cbuf[m + 1] : CT(0);
-            b2 += (m + 2 <= lane) ? to_ct(rb[m + 2]) * cbuf[m + 2] : CT(0);
-            b3 += (m + 3 <= lane) ? to_ct(rb[m + 3]) * cbuf[m + 3] : CT(0);
-          }
-        } else {
-#pragma unroll
-          for (int d = 0; d < 32; d += 4) {
-            b0 += (d < 32 - lane) ? to_ct(row[d]) * cbuf[lane + d] : CT(0);
-            b1 += (d + 1 < 32 - lane) ? to_ct(row[d + 1]) * cbuf[lane + d + 1] : CT(0);
-            b2 += (d + 2 < 32 - lane) ? to_ct(row[d + 2]) * cbuf[lane + d + 2] : CT(0);
-            b3 += (d + 3 < 32 - lane) ? to_ct(row[d + 3]) * cbuf[lane + d + 3] : CT(0);
-          }
-        }
-        y[i] = (b0 + b1) + (b2 + b3);
-      }
-      __syncthreads();
-      // every thread is done with stage st: refill it
-      if (tid == 0 && s + NS < nb) {
+      for (int j = NREG - 1; j > 0; --j) yr[j] = yr[j - 1];
+      yr[0] = v;
+      if (warp == 0) y[32 * K + lane] = v;
+      // every warp has read slab st before the barrier: refill it
+      if (tid == 0 && !direct && s + NS < nb) {
         const int Kb = dir == 0 ? s + NS : nb - 1 - (s + NS);
-        fence_proxy_async();
         tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
       }
     }
-    gcount += nb;
+    if (!direct) gcount += nb;
+    __syncthreads();  // y complete before the next pass reads it
   }
   return true;
-}
-
-// Banded Cholesky solve L L^T delta = r by warp 0. y[OFF + i] holds r on entry
-// and delta on exit; y[0, OFF) and y[OFF+npad, OFF+npad+W+16) must be zero.
-// Slabs stream through an NS-stage ring of shared memory with bulk copies
-// (cp.async.bulk + mbarrier), up to NS blocks ahead of the block being solved.
-// gcount: running slab count of this CTA (selects stage and parity).
-template <typename T, typename CT, int NS>
-__device__ bool band_solve_warp(const T *slabF, const T *slabB, int nb, int W, CT *y, int OFF,
-                                CT *cbuf, T *ring, int ring_stride, uint64_t *mbar,
-                                uint32_t &gcount, int64_t timeout_ns) {
-  const int lane = threadIdx.x & 31;
-  const int S = slab_stride(W, (int)sizeof(T));
-  const int64_t slab = (int64_t)32 * S;
-  const uint32_t bytes = (uint32_t)(slab * sizeof(T));
-  bool ok = true;
-  for (int dir = 0; dir < 2; ++dir) {
-    const T *base = dir == 0 ? slabF : slabB;
-    // block processed at step s: forward K = s, backward K = nb-1-s
-    int issued = 0;
-    if (lane == 0) {
-      for (; issued < NS && issued < nb; ++issued) {
-        const int Kb = dir == 0 ? issued : nb - 1 - issued;
-        const uint32_t st = (gcount + issued) % NS;
-        fence_proxy_async();
-        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
-      }
-    }
-    issued = __shfl_sync(0xffffffffu, issued, 0);
-    int s = 0;
-    for (; s < nb; ++s) {
-      const uint32_t g = gcount + s;
-      const uint32_t st = g % NS;
-      const uint32_t par = (g / NS) & 1u;
-      if (!mbar_wait(&mbar[st], par, timeout_ns)) { ok = false; break; }
-      const T *row = ring + st * ring_stride + lane * S;
-      const int K = dir == 0 ? s : nb - 1 - s;
-      if (dir == 0) band_fwd_block<T, CT>(row, y + OFF, 32 * K + lane, W, lane, cbuf);
-      else band_bwd_block<T, CT>(row, y + OFF, 32 * K + lane, W, lane, cbuf);
-      // refill the stage just consumed
-      if (issued < nb) {
-        if (lane == 0) {
-          const int Kb = dir == 0 ? issued : nb - 1 - issued;
-          const uint32_t st2 = (gcount + issued) % NS;
-          fence_proxy_async();
-          tma_load_1d(ring + st2 * ring_stride, base + Kb * slab, bytes, &mbar[st2]);
-        }
-        ++issued;
-      }
-    }
-    if (!ok) {
-      // wait (bounded) for the copies still in flight before giving up
-      for (int s2 = s; s2 < issued; ++s2) {
-        const uint32_t g = gcount + s2;
-        mbar_wait(&mbar[g % NS], (g / NS) & 1u, timeout_ns);
-      }
-      gcount += issued;
-      return false;
-    }
-    gcount += nb;
-  }
-  return ok;
 }
 
 // m steps of textbook CG on A_p d = r from d = 0 (all threads). A_p in ELL
@@ -1035,39 +834,70 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
 
 // r_p = b[Omega_p] - A[Omega_p, :] x for the rows of one subdomain (thread t:
 // rows t, t + NT, ...), written to rhs in the compute type; accumulates
-// ||r||^2 over Omega_p and over its owned rows. KC > 0: ELL width at compile
-// time, so every column / value / x load of a row issues before the FMAs.
+// ||r||^2 over Omega_p and over its owned rows, and records for every owned
+// row the x value used for its diagonal column (xg, used by the update).
+// KC > 0: ELL width known at compile time; rows are then taken two at a time
+// so that both rows' index / value loads, and then both rows' x loads, are in
+// flight together (the gather is bound by memory latency, not bandwidth).
 template <int KC, typename CT, int NT>
 __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, int K,
                                             const double *xcur, bool async, CT *rhs,
                                             double &a_loc, double &a_own) {
   const int64_t eb = D.row_off * K;
-  for (int i = threadIdx.x; i < D.npad; i += NT) {
-    double r = 0.0;
-    if (i < D.n) {
-      const int g = S.gidx[D.row_off + i];
-      r = S.b[g];
-      if constexpr (KC > 0) {
-        int cols[KC];
-        double vals[KC], xs[KC];
+  if constexpr (KC > 0) {
+    for (int i0 = threadIdx.x; i0 < D.npad; i0 += 2 * NT) {
+      int cols[2][KC], g[2];
+      double vals[2][KC], xs[2][KC], bb[2];
+      bool live[2], own[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + h * NT;
+        live[h] = i < D.n;
+        const int ii = live[h] ? i : 0;
+        g[h] = S.gidx[D.row_off + ii];
+        own[h] = live[h] && S.ownf[D.row_off + ii];
 #pragma unroll
         for (int k = 0; k < KC; ++k) {
-          const int64_t e = eb + (int64_t)k * D.npad + i;
-          cols[k] = S.rcol[e];
-          vals[k] = S.rval[e];
+          const int64_t e = eb + (int64_t)k * D.npad + ii;
+          cols[h][k] = S.rcol[e];
+          vals[h][k] = S.rval[e];
         }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        bb[h] = S.b[g[h]];
 #pragma unroll
         for (int k = 0; k < KC; ++k)
-          xs[k] = async ? ld_relaxed_f64(xcur + cols[k]) : __ldcg(xcur + cols[k]);
+          xs[h][k] = async ? ld_relaxed_f64(xcur + cols[h][k]) : __ldcg(xcur + cols[h][k]);
+      }
 #pragma unroll
-        for (int k = 0; k < KC; ++k) r -= vals[k] * xs[k];
-        if (S.ownf[D.row_off + i]) {
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + h * NT;
+        if (i >= D.npad) continue;
+        double r = 0.0;
+        if (live[h]) {
+          r = bb[h];
           double xd = 0.0;
 #pragma unroll
-          for (int k = 0; k < KC; ++k) xd = cols[k] == g ? xs[k] : xd;
-          S.xg[D.row_off + i] = xd;
+          for (int k = 0; k < KC; ++k) {
+            r -= vals[h][k] * xs[h][k];
+            xd = cols[h][k] == g[h] ? xs[h][k] : xd;
+          }
+          if (own[h]) {
+            S.xg[D.row_off + i] = xd;
+            a_own += r * r;
+          }
+          a_loc += r * r;
         }
-      } else {
+        rhs[i] = (CT)r;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < D.npad; i += NT) {
+      double r = 0.0;
+      if (i < D.n) {
+        const int g = S.gidx[D.row_off + i];
+        r = S.b[g];
         double xd = 0.0;
         for (int k = 0; k < K; ++k) {
           const int64_t e = eb + (int64_t)k * D.npad + i;
@@ -1076,12 +906,14 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
           r -= S.rval[e] * xv;
           xd = c == g ? xv : xd;
         }
-        if (S.ownf[D.row_off + i]) S.xg[D.row_off + i] = xd;
+        if (S.ownf[D.row_off + i]) {
+          S.xg[D.row_off + i] = xd;
+          a_own += r * r;
+        }
+        a_loc += r * r;
       }
-      a_loc += r * r;
-      if (S.ownf[D.row_off + i]) a_own += r * r;
+      rhs[i] = (CT)r;
     }
-    rhs[i] = (CT)r;
   }
 }
 
@@ -1090,25 +922,24 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 // --------------------------------------------------------------------------
 
 constexpr int kBandStages = 8;  // ring capacity; Launch::nstages of them are used
-constexpr int kYPad = 48;  // zero tail of y beyond W (vector overrun of the last chunk)
 
 template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
-  // band: ring | y | cbuf ; cg: r p q d ; ilu: r z p q d
+  // band: ring | y | t | partials ; cg: r p q d ; ilu: r z p q d ; staged cg: A_p | p
   static __host__ __device__ size_t ring_stride(int Wmax) {
-    const size_t b = (size_t)slab_stride(Wmax, (int)sizeof(T)) * 32 * sizeof(T);
+    const size_t b = (size_t)Wmax * 32 * sizeof(T);
     return ((b + 127) / 128) * 128 / sizeof(T);
   }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
-    return ((size_t)(2 * Wmax + npad_max + kYPad) + 31) / 32 * 32;
+    return ((size_t)npad_max + 31) / 32 * 32;
   }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
   static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax, int nstages) {
     if (KIND == kBand) {
       size_t b = (size_t)nstages * ring_stride(Wmax) * sizeof(T);
-      b += ylen(Wmax, npad_max) * sizeof(CT);
-      b += (64 + NT) * sizeof(CT);  // cbuf, per-warp partials
+      b += 2 * ylen(Wmax, npad_max) * sizeof(CT);  // y (r / delta), t
+      b += 2 * NT * sizeof(CT);                     // partials, two buffers
       return b;
     }
     if (KIND == kCGS) {
@@ -1148,15 +979,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
 
   // shared-memory carve-up
   T *ring = nullptr;
-  CT *ybuf = nullptr, *cbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
+  CT *ybuf = nullptr, *tbuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
      *v4 = nullptr;
   int ring_stride = 0;
-  const int OFF = L.Wmax;
   if (KIND == kBand) {
     ring_stride = (int)SM::ring_stride(L.Wmax);
     ring = reinterpret_cast<T *>(smem);
     ybuf = reinterpret_cast<CT *>(smem + (size_t)L.nstages * ring_stride * sizeof(T));
-    cbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
+    tbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
+    pbuf = tbuf + SM::ylen(L.Wmax, L.npad_max);
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
     v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
@@ -1170,8 +1001,6 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     v4 = KIND == kILU ? base + 4 * vl : nullptr;
   }
   uint32_t gcount = 0;
-  if (KIND == kBand)
-    for (int e = tid; e < 64; e += NT) cbuf[e] = CT(0);  // cbuf[32, 64) stays zero
   if (KIND == kBand || KIND == kCGS) {
     if (tid == 0) {
       for (int s = 0; s < L.nstages; ++s) mbar_init(&s_mbar[s], 1);
@@ -1198,7 +1027,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     const SysDesc &S = s_sys;
     const SubDesc &D = s_sub;
     const int K = S.K;
-    CT *rhs = KIND == kBand ? ybuf + OFF : v0;
+    CT *rhs = KIND == kBand ? ybuf : v0;
     uint64_t t0 = 0, t1 = 0, t2 = 0;
     if (tid == 0) t0 = gtimer();
     if (KIND == kCGS && tid == 0) {
@@ -1211,11 +1040,6 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
                    : "memory");
       bulk_copy_nobar_arrive(smem, reinterpret_cast<const float *>(S.lval) + D.row_off * K, bv, &s_mbar[0]);
       bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.lcol16 + D.row_off * K, bc, &s_mbar[0]);
-    }
-    if (KIND == kBand) {
-      // zero the halo of y (head and tail)
-      for (int e = tid; e < OFF; e += NT) ybuf[e] = CT(0);
-      for (int e = tid; e < L.Wmax + kYPad; e += NT) ybuf[OFF + D.npad + e] = CT(0);
     }
     double a_loc = 0.0, a_own = 0.0;
     if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
@@ -1230,11 +1054,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kBand) {
       __syncthreads();
       const T *fac = reinterpret_cast<const T *>(S.fac);
-      const int64_t slab = (int64_t)32 * slab_stride(D.W, (int)sizeof(T));
+      const int64_t slab = (int64_t)32 * D.W;
       const int nb = D.npad / 32;
-      const bool ok = band_solve_cta<T, CT, NT>(
-          fac + D.fac_off, fac + D.fac_off + nb * slab, nb, D.W, ybuf + OFF, cbuf, cbuf + 64, ring,
-          ring_stride, s_mbar, gcount, L.timeout_ns, L.nstages);
+      const T *F = fac + D.fac_off;
+      const bool ok = band_solve_m<T, CT, NT>(F, F + nb * slab, F + 2 * nb * slab, nb, D.W, ybuf,
+                                              tbuf, pbuf, ring, ring_stride, s_mbar, gcount,
+                                              L.timeout_ns, L.nstages, L.band_direct != 0);
       if (!ok) {
         if (tid == 0) set_error(L.ctl, kETIMEOUT, 2);
         return false;
@@ -1534,10 +1359,26 @@ out:
 // host-side launchers
 // --------------------------------------------------------------------------
 
+// The dynamic shared-memory limit of a kernel is process-wide state. Every
+// caller sets it to the device's opt-in maximum (the same value each time), so
+// host threads setting it concurrently cannot lower it under each other's
+// launches; each launch passes its actual size.
+static cudaError_t allow_max_smem(const void *fn) {
+  int dev = 0, maxb = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxb, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);  // the opt-in limit covers static + dynamic
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             maxb - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 template <int KIND, typename T, int NT>
 static cudaError_t launch_main_t(const Launch &L, int grid, size_t smem, cudaStream_t stream) {
   auto fn = ras_main_kernel<KIND, T, NT>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void *)fn);
   if (e != cudaSuccess) return e;
   Launch Lc = L;
   void *args[] = {&Lc};
@@ -1547,8 +1388,7 @@ static cudaError_t launch_main_t(const Launch &L, int grid, size_t smem, cudaStr
 template <int KIND, typename T, int NT>
 static int occupancy_t(size_t smem) {
   auto fn = ras_main_kernel<KIND, T, NT>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
+  if (allow_max_smem((const void *)fn) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem) != cudaSuccess) return 0;
   return nb;
@@ -1614,6 +1454,17 @@ cudaError_t launch_residual(const Launch &L, int nitems, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+__global__ void fill_kernel(double *x, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t stream) {
+  fill_kernel<<<256, 256, 0, stream>>>(x, v, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copyback(const Launch &L, int nitems, cudaStream_t stream) {
   ras_copyback_kernel<<<nitems, 128, 0, stream>>>(L);
   return cudaGetLastError();
@@ -1622,8 +1473,7 @@ cudaError_t launch_copyback(const Launch &L, int nitems, cudaStream_t stream) {
 cudaError_t launch_band_chol(const BandJob *jobs, int njobs, int max_w, double *band,
                              GridCtl *ctl, cudaStream_t stream) {
   const size_t smem = (size_t)(max_w + 1) * (max_w + 1) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(band_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = allow_max_smem((const void *)band_chol_kernel);
   if (e != cudaSuccess) return e;
   band_chol_kernel<<<njobs, 256, smem, stream>>>(jobs, band, ctl);
   return cudaGetLastError();

@@ -1,0 +1,87 @@
+"""Full-size workloads, checked where the oracle cannot run them to the end:
+sampled index maps bit-exact, the first synchronous iterations against the
+oracle's, and the true FP64 relative residual (oracle residual routine) of
+every converged result."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2003_05361_gb300 as ras
+import problems
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def solve(ctx, A, b, mode, tol=1e-8, max_updates=0):
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    info = ras.ras_solve(ctx, torch.tensor(b, device="cuda"), x, tol, mode, max_updates)
+    return x.cpu().numpy(), info
+
+
+def relres(A, b, x):
+    _, rn = oracle.residual(A, b, x)
+    return rn / np.linalg.norm(b)
+
+
+def test_config2_full_size():
+    # 2D Poisson 1024^2, uniform b seed 1, regular 16x16, overlap 4, CG-20
+    N = 1024
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 1)
+    part = ras.ras_partition_regular2d(N, N, 16, 16)
+    ctx64 = ras.ras_setup(A, part, 256, 4, ras.RAS_LOCAL_CG, ras.RAS_FP64, 20)
+    # first two synchronous iterates against the oracle's (FP64 CG, 1e-9)
+    xo, _, _ = oracle.ras_sync(A, b, part, 256, 4, oracle.CG, oracle.FP64, 20, tol=0.0,
+                               max_iter=2, nthreads=8, allow_noconv=True)
+    x, info = solve(ctx64, A, b, ras.RAS_SYNC, max_updates=2)
+    assert info.iterations == 2
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+    ras.ras_destroy(ctx64)
+    ctx = ras.ras_setup(A, part, 256, 4, ras.RAS_LOCAL_CG, ras.RAS_FP32, 20)
+    for mode in (ras.RAS_ASYNC, ras.RAS_SYNC):
+        x, info = solve(ctx, A, b, mode)
+        assert info.status == 0 and relres(A, b, x) < 1e-8
+    ras.ras_destroy(ctx)
+
+
+def test_config3_full_size():
+    # 3D Poisson 128^3, uniform b seed 3, BFS-growth 512 parts (seed 3),
+    # overlap 1, ILU(0)-PCG in FP32 with FP64 outer residual / update
+    N = 128
+    A = problems.poisson3d(N)
+    b = problems.rhs_uniform(A.n, 3)
+    part = ras.ras_partition_bfs(A, 512, 3)
+    ctx = ras.ras_setup(A, part, 512, 1, ras.RAS_LOCAL_ILU0_CG, ras.RAS_FP32, 10)
+    for p in (0, 137, 511):
+        om, ow, ifc = ras.ras_get_maps(ctx, p)
+        om2, ow2, ifc2 = oracle.overlap(A, part, 512, p, 1)
+        assert np.array_equal(om, om2) and np.array_equal(ow, ow2) and np.array_equal(ifc, ifc2)
+    for mode in (ras.RAS_ASYNC, ras.RAS_SYNC):
+        x, info = solve(ctx, A, b, mode)
+        assert info.status == 0, info.as_dict()
+        assert relres(A, b, x) < 1e-8
+    ras.ras_destroy(ctx)
+
+
+def test_config4_full_size():
+    # variable-coefficient diffusion 2048^2, k = exp(GRF, sigma 1, ell 1/32),
+    # regular 32x32, overlap 4, banded Cholesky stored in FP32 and BF16
+    N = 2048
+    k = problems.grf_coefficient(N, 4)
+    A = problems.diffusion2d(N, k)
+    b = problems.rhs_uniform(A.n, 4)
+    part = ras.ras_partition_regular2d(N, N, 32, 32)
+    sols = {}
+    for prec in (ras.RAS_FP32, ras.RAS_BF16_STORE):
+        ctx = ras.ras_setup(A, part, 1024, 4, ras.RAS_LOCAL_BANDCHOL, prec)
+        x, info = solve(ctx, A, b, ras.RAS_SYNC)
+        assert info.status == 0, info.as_dict()
+        assert relres(A, b, x) < 1e-8
+        sols[prec] = x
+        ras.ras_destroy(ctx)
+    # both reach the same FP64 fixed point: their difference is bounded by
+    # what two residuals below 1e-8 allow; report-level check
+    d = np.linalg.norm(sols[ras.RAS_FP32] - sols[ras.RAS_BF16_STORE]) / np.linalg.norm(sols[ras.RAS_FP32])
+    assert d < 1e-3

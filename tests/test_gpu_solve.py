@@ -172,6 +172,23 @@ def test_async_one_subdomain_per_cta_large_overlap():
         assert true_relres(A, b, x) < 1e-8
 
 
+@pytest.mark.parametrize("kind,prec", [(CG, F32), (ILU, F32), (BAND, F32)])
+def test_autotune_then_solve(kind, prec):
+    N = 192
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 4)
+    part = ras.ras_partition_regular2d(N, N, 3, 3)
+    ctx = ras.ras_setup(A, part, 9, 2, kind, prec, 10)
+    xs = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    r = ras.ras_autotune(ctx, xs, ras.RAS_SYNC, 30, True)
+    assert r.candidates >= 1 and r.cta_threads in (256, 512) and r.inner_iters >= 1
+    launch = ras.ras_get_launch(ctx)
+    assert launch["cta_threads"] == r.cta_threads and launch["inner_iters"] == r.inner_iters
+    x, info = gpu_solve(A, b, part, 9, 2, kind, prec, 10, ctx=ctx)
+    assert info.status == 0 and true_relres(A, b, x) < 1e-8
+    ras.ras_destroy(ctx)
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_single_subdomain_one_iteration():
