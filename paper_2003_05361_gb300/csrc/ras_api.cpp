@@ -453,16 +453,34 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (nt_pref <= 0) nt_pref = (int)env_int("RAS_CTA_THREADS", 256);
+  if (nt_pref <= 0) nt_pref = (int)env_int("RAS_CTA_THREADS", 0);  // 0: per-kind default
   pl.nt = main_threads(kind, nt_pref);
   pl.Wmax = Wmax;
   pl.npad_max = npad_max;
   pl.kmax = kmax;
-  pl.nstages = (int)std::min<int64_t>(8, std::max<int64_t>(2, env_int("RAS_BAND_STAGES", 4)));
+  // band: copy pipeline depth (chain steps in flight), reduced until the
+  // shared memory fits, and down to 3 when that lets two CTAs share an SM
+  // band: copy pipeline depth (chain steps in flight, 6 or 4): 4 when 6 does
+  // not fit, or when 4 lets more CTAs share an SM and there are subdomains
+  // enough to use them
+  pl.nstages = env_int("RAS_BAND_STAGES", 6) >= 6 ? 6 : 4;
   pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax, pl.nstages);
+  if (kind == kBand && pl.nstages == 6 && pl.smem + 4096 > (size_t)max_smem) {
+    pl.nstages = 4;
+    pl.smem = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax, pl.nstages);
+  }
   if (pl.smem + 4096 > (size_t)max_smem) return RAS_ENOTSUP;
-  const int occ = main_occupancy(kind, prec, pl.nt, pl.smem);
+  int occ = main_occupancy(kind, prec, pl.nt, pl.smem);
   if (occ <= 0) return RAS_ENOTSUP;
+  if (kind == kBand && pl.nstages == 6 && (int64_t)items.size() > (int64_t)occ * nsm) {
+    const size_t sm4 = main_smem_bytes(kind, prec, pl.nt, Wmax, npad_max, kmax, 4);
+    const int occ4 = main_occupancy(kind, prec, pl.nt, sm4);
+    if (occ4 > occ) {
+      pl.nstages = 4;
+      pl.smem = sm4;
+      occ = occ4;
+    }
+  }
   int64_t cap = (int64_t)occ * nsm;
   const int64_t lim = env_int("RAS_MAX_CTAS", 0);
   if (lim > 0) cap = std::min<int64_t>(cap, lim);
@@ -687,7 +705,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     d.n = (int32_t)mp.omega.size();
     d.npad = (d.n + 31) / 32 * 32;
     d.n_own = (int32_t)owned_lists[p].size();
-    d.W = std::max(mp.w, 1);
+    d.W = (std::max(mp.w, 1) + 3) / 4 * 4;  // band records: W a multiple of 4
     d.row_off = rows;
     d.own_off = owns;
     d.fac_off = fac;
@@ -698,7 +716,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     nbrs += d.n_nbr;
     if (kind == RAS_LOCAL_BANDCHOL) {
       if (mp.w > 160) return RAS_ENOTSUP;
-      fac += 2ll * (d.npad / 32) * 32 * d.W + (int64_t)(d.npad / 32) * 528;
+      fac += 2ll * (d.npad / 32) * 32 * (d.W + 32);  // forward and backward records
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
@@ -977,7 +995,6 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.persist = 1;
   L.kmax = pl.kmax;
   L.nstages = pl.nstages;
-  L.band_direct = (int32_t)env_int("RAS_BAND_DIRECT", 0);
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   const int nitems = (int)pl.items.size();
@@ -1282,7 +1299,6 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   L.persist = 0;
   L.kmax = sc.plan.kmax;
   L.nstages = sc.plan.nstages;
-  L.band_direct = (int32_t)env_int("RAS_BAND_DIRECT", 0);
   std::memset(sc.h_ctl, 0, sizeof(GridCtl));
   sc.h_ctl->remaining = running;
   const int nitems = (int)sc.plan.items.size();
@@ -1384,6 +1400,7 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
   }
   for (int m : ms) {
     if (kind == RAS_LOCAL_BANDCHOL) {
+      cands.push_back({kBand, 128, m});
       cands.push_back({kBand, 256, m});
     } else {
       cands.push_back({kind, 256, m});

@@ -144,7 +144,7 @@ struct Launch {
   int32_t persist;             // async: keep polling until every system is done
   int32_t kmax;                // largest ELL width over the launch
   int32_t nstages;             // band: slab ring depth (2..8)
-  int32_t band_direct;         // band: 1 = warps read their slab slices from global memory
+  int32_t pad2_;
 };
 
 }  // namespace ras

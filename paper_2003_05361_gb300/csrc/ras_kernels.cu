@@ -245,6 +245,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int64_
   return true;
 }
 
+// 16-byte asynchronous global -> shared copies (L2 only), tracked per thread
+// by commit groups.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
 // setup: banded Cholesky (FP64)
 // --------------------------------------------------------------------------
@@ -331,11 +341,13 @@ __global__ void __launch_bounds__(256) band_chol_kernel(const BandJob *jobs, dou
 // and backward substitution with U = L^T
 //   z_K = t'_K - M'_K z[32K+32, 32K+32+W),  t'_K = U_KK^{-1} y_K,
 //   M'_K = U_KK^{-1} U[K rows, 32K+32 .. 32K+32+W)                   (32 x W).
-// Per subdomain the storage is: nb forward slabs M_K, nb backward slabs M'_K
-// (each column-major, entry (l, c) at c*32 + l), then nb inverse diagonal
-// blocks L_KK^{-1} packed by diagonals (entry (l, l-e) at off(e) + l - e with
-// off(e) = 32e - e(e-1)/2, 528 entries per block); U_KK^{-1}[l][l+e] =
-// L_KK^{-1}[l+e][l] is read from the same storage at off(e) + l.
+// Per subdomain the storage is nb forward records, then nb backward records,
+// each a column-major 32 x (32 + W) matrix (entry (l, j) at j*32 + l):
+//   forward  record K = [ L_KK^{-1} | M_K  ],
+//   backward record K = [ U_KK^{-1} | M'_K ],  U_KK^{-1} = (L_KK^{-1})^T,
+// so that a chain step reads one contiguous record and every one of its
+// 32 + W columns is applied to one broadcast value (the step's own right-hand
+// side for the first 32, a finished window row for the rest).
 template <typename T>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
@@ -375,11 +387,13 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) X[r][m] = col[r];
   }
   __syncwarp();
-  const int64_t slab = (int64_t)32 * W;
-  T *F = fac + jb.fac_off + (int64_t)K * slab;
-  T *Bk = fac + jb.fac_off + (int64_t)nb * slab + (int64_t)K * slab;
-  T *I = fac + jb.fac_off + 2 * (int64_t)nb * slab + (int64_t)K * 528;
-  for (int e = 0; e <= l; ++e) I[32 * e - e * (e - 1) / 2 + (l - e)] = from_double<T>(X[l][l - e]);
+  const int64_t rec = (int64_t)32 * (W + 32);
+  T *F = fac + jb.fac_off + (int64_t)K * rec;
+  T *Bk = fac + jb.fac_off + (int64_t)nb * rec + (int64_t)K * rec;
+  for (int m = 0; m < 32; ++m) {
+    F[m * 32 + l] = from_double<T>(X[l][m]);   // L_KK^{-1}[l][m]
+    Bk[m * 32 + l] = from_double<T>(X[m][l]);  // U_KK^{-1}[l][m]
+  }
   // M_K[l][c] = sum_{m <= l} Linv[l][m] L[32K+m][32K-W+c]
   for (int c = 0; c < W; ++c) {
     const int col = 32 * K - W + c;
@@ -389,7 +403,7 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
         const int r = 32 * K + m;
         if (r < n && col >= r - w) s += X[l][m] * Bd[(int64_t)r * ld + (col - r + w)];
       }
-    F[(int64_t)c * 32 + l] = from_double<T>(s);
+    F[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
   }
   // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c],  U[a][b] = L[b][a]
   for (int c = 0; c < W; ++c) {
@@ -400,7 +414,7 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
         const int col = 32 * K + m;
         if (col >= r - w) s += X[m][l] * Bd[(int64_t)r * ld + (col - r + w)];
       }
-    Bk[(int64_t)c * 32 + l] = from_double<T>(s);
+    Bk[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
   }
 }
 
@@ -506,134 +520,130 @@ __global__ void __launch_bounds__(128) ras_copyback_kernel(Launch L) {
 // local solvers
 // --------------------------------------------------------------------------
 
-// Offset of diagonal e in a packed inverse diagonal block (528 entries).
-__device__ __forceinline__ int diag_off(int e) { return 32 * e - e * (e - 1) / 2; }
-
-// t = blockdiag(L_KK^{-1}) v (fwd) or blockdiag(U_KK^{-1}) v (!fwd) for every
-// block, warps taking blocks round-robin; the inverse blocks are read straight
-// from global memory (coalesced along each diagonal), four blocks per warp in
-// flight.
-template <typename T, typename CT, int NT, bool FWD>
-__device__ __forceinline__ void band_diag_apply(const T *__restrict__ I, int nb, const CT *v,
-                                                CT *t) {
-  constexpr int NW = NT / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int K0 = warp; K0 < nb; K0 += 4 * NW) {
-    CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
-#pragma unroll
-    for (int e = 0; e < 32; ++e) {
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int K = K0 + h * NW;
-        if (K < nb) {
-          if (FWD) {
-            if (e <= lane)
-              acc[h] += to_ct(I[(int64_t)K * 528 + diag_off(e) + lane - e]) * v[32 * K + lane - e];
-          } else {
-            if (e <= 31 - lane)
-              acc[h] += to_ct(I[(int64_t)K * 528 + diag_off(e) + lane]) * v[32 * K + lane + e];
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int K = K0 + h * NW;
-      if (K < nb) t[32 * K + lane] = acc[h];
-    }
-  }
+// Four consecutive values from 16-byte aligned shared memory.
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2 *>(p);
+  const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// Banded Cholesky solve L L^T delta = r by the whole CTA: t = blockdiag(Linv) r;
-// forward chain y_K = t_K - M_K y_window; t' = blockdiag(Uinv) y; backward
-// chain z_K = t'_K - M'_K z_window. In a chain step every warp takes a slice
-// of the W window columns (the window values, the last few finished blocks,
-// stay in registers and are broadcast by warp-uniform shuffles), writes its
-// 32 partial sums, and after ONE barrier every warp adds the partials in the
-// same fixed order, so all warps hold identical y_K. y[0..npad) holds r on
-// entry and delta on exit; t is an npad scratch vector; part holds
-// 2 * NT partials. The slabs M_K / M'_K stream through an NS-stage ring with
-// bulk copies issued by thread 0 (the ring is written only by the copies and
-// read only before the barrier that precedes each refill, so no proxy fence
-// is needed).
-template <typename T, typename CT, int NT>
-__device__ bool band_solve_m(const T *F, const T *Bs, const T *I, int nb, int W, CT *y, CT *t,
-                             CT *part, T *ring, int ring_stride, uint64_t *mbar, uint32_t &gcount,
-                             int64_t timeout_ns, const int NS, const bool direct) {
+// Columns of a band record each warp of an NW-warp CTA takes per chain step:
+// ceil((W + 32) / NW) rounded up to a multiple of 4 (W itself is a multiple of
+// 4), so every warp's first column, and the broadcast values it reads, are
+// 16-byte aligned.
+__host__ __device__ inline int band_cols_per_warp(int W, int NW) {
+  return ((W + 32 + NW - 1) / NW + 3) / 4 * 4;
+}
+
+// Banded Cholesky solve L L^T delta = r by the whole CTA as two block chains:
+// forward y_K = L_KK^{-1} r_K - M_K y_window, backward
+// z_K = U_KK^{-1} y_K - M'_K z_window. A chain step applies the 32 + W columns
+// of one record (see band_layout_kernel) to broadcast values: column j < 32 to
+// row 32K + j of the step's own input (r in the forward pass, y in the
+// backward pass, read from y before the step overwrites it), window column
+// j = 32 + c to finished row 32K - W + c (forward) or 32K + 32 + c (backward).
+// Warp w takes the contiguous columns [w tw, (w+1) tw) (band_cols_per_warp)
+// and writes its 32 partial sums; after ONE barrier every warp adds the
+// partials in the same fixed order, so all warps hold identical y_K. Window
+// sums enter with a minus sign.
+// Each warp streams its own columns of record s + D - 1 with 16-byte cp.async
+// copies into a private D-slot ring while it computes step s; a copy is waited
+// for by the thread that issued it and published to the warp by __syncwarp,
+// so the chain needs no mbarrier and no second barrier. A slot is refilled one
+// step after it was read, behind that step's barrier. Each warp keeps its own
+// copy of the last 8 finished blocks in win (row g at g & 255, stored twice,
+// at +0 and +256, so that a warp's window rows are one unwrapped run); window
+// rows outside [0, npad) meet zero operator columns and read zero-initialised
+// slots. y[0..npad) holds r on entry and delta on exit; part holds 2 NT
+// partials.
+template <typename T, typename CT, int NT, int D>
+__device__ void band_solve_chain(const T *__restrict__ F, const T *__restrict__ Bs, int nb, int W,
+                                 int twm, CT *y, CT *part, CT *win, T *ring) {
   constexpr int NW = NT / 32;
-  constexpr int NREG = 6;  // finished blocks kept in registers (W <= 160)
+  constexpr int V = 16 / (int)sizeof(T);  // values per 16-byte copy
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t slab = (int64_t)32 * W;
-  const uint32_t bytes = (uint32_t)(slab * sizeof(T));
-  const int tw = (W + NW - 1) / NW;
-  const int c0 = warp * tw;
-  const int c1 = c0 + tw < W ? c0 + tw : W;
+  const int NI = W + 32;
+  const int tw = band_cols_per_warp(W, NW);
+  const int j0 = warp * tw < NI ? warp * tw : NI;
+  const int j1 = j0 + tw < NI ? j0 + tw : NI;
+  const int cnt = j1 - j0;
+  const int nd = (j1 < 32 ? j1 : 32) - (j0 < 32 ? j0 : 32);  // own-input columns
+  const int nchunk = cnt * 32 / V;  // 16-byte chunks of this warp's columns
+  const int64_t rec = (int64_t)32 * NI;
+  const int slot_len = twm * 32;
+  T *rw = ring + (size_t)warp * D * slot_len;
+  CT *wy = win + warp * 512;  // two copies of an 8-block ring: reads never wrap
   for (int dir = 0; dir < 2; ++dir) {
-    const T *base = dir == 0 ? F : Bs;
-    if (tid == 0 && !direct) {
-      const int pro = nb < NS ? nb : NS;
-      for (int j = 0; j < pro; ++j) {
-        const int Kb = dir == 0 ? j : nb - 1 - j;
-        tma_load_1d(ring + ((gcount + j) % NS) * ring_stride, base + Kb * slab, bytes,
-                    &mbar[(gcount + j) % NS]);
+    const T *src_l = (dir == 0 ? F : Bs) + (int64_t)j0 * 32 + lane * V;
+    T *dst_l = rw + lane * V;
+    // copies of chain step s into ring slot sl (one commit group, maybe empty)
+    auto issue = [&](int s, int sl) {
+      if (s < nb) {
+        const T *src = src_l + (dir == 0 ? s : nb - 1 - s) * rec;
+        T *dst = dst_l + sl * slot_len;
+        for (int q0 = 0; q0 < nchunk; q0 += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u * 32 + lane < nchunk) cp_async16(dst + (q0 + u * 32) * V, src + (q0 + u * 32) * V);
+        }
       }
-    }
-    if (dir == 0) band_diag_apply<T, CT, NT, true>(I, nb, y, t);
-    else band_diag_apply<T, CT, NT, false>(I, nb, y, t);
-    __syncthreads();
-    CT yr[NREG];
+      cp_async_commit();
+    };
 #pragma unroll
-    for (int j = 0; j < NREG; ++j) yr[j] = CT(0);
+    for (int q = 0; q < 16; ++q) wy[q * 32 + lane] = CT(0);
+#pragma unroll
+    for (int s = 0; s < D - 1; ++s) issue(s, s);
+    int cur = 0;  // slot of step s
     for (int s = 0; s < nb; ++s) {
-      const uint32_t g = gcount + s;
-      const uint32_t st = g % NS;
-      const bool ok = direct ? true : mbar_wait(&mbar[st], (g / NS) & 1u, timeout_ns);
+      issue(s + D - 1, cur == 0 ? D - 1 : cur - 1);
+      asm volatile("cp.async.wait_group %0;" ::"n"(D - 1) : "memory");
+      __syncwarp();
       const int K = dir == 0 ? s : nb - 1 - s;
-      CT acc = CT(0);
-      if (ok) {
-        // slab of block K: from the ring, or straight from global memory
-        const T *sl = direct ? base + K * slab : ring + st * ring_stride;
-        for (int c = c0; c < c1; ++c) {
-          // window row of column c and its distance (in blocks) from block K
-          const int grow = dir == 0 ? 32 * K - W + c : 32 * K + 32 + c;
-          const int dist = dir == 0 ? K - (grow >> 5) : (grow >> 5) - K;  // >= 1
-          CT src = CT(0);
+      const T *sl = rw + cur * slot_len + lane;
+      CT a[4] = {CT(0), CT(0), CT(0), CT(0)};
+      int ii = 0;
+      if (nd > 0) {
+        const CT *ys = y + 32 * K + j0;  // own input rows 32K + j
+        for (; ii < nd; ii += 4) {
+          CT bv[4];
+          ld4(ys + ii, bv);
 #pragma unroll
-          for (int j = 0; j < NREG; ++j) src = (dist - 1 == j) ? yr[j] : src;
-          const CT yv = __shfl_sync(0xffffffffu, src, grow & 31);
-          acc += to_ct(sl[c * 32 + lane]) * yv;
+          for (int u = 0; u < 4; ++u)
+            if (ii + u < nd) a[u] += to_ct(sl[(ii + u) * 32]) * bv[u];
+        }
+        ii = nd;
+      }
+      if (ii < cnt) {
+        // window row of column j: 32K - W - 32 + j (forward), 32K + j (backward)
+        const int g0 = (dir == 0 ? 32 * K - W - 32 : 32 * K) + j0;
+        const CT *ws = wy + (g0 & 255);
+        for (; ii < cnt; ii += 4) {
+          CT bv[4];
+          ld4(ws + ii, bv);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (ii + u < cnt) a[u] -= to_ct(sl[(ii + u) * 32]) * bv[u];
         }
       }
       CT *pb = part + (s & 1) * NT;
-      pb[warp * 32 + lane] = acc;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0 && !direct)
-          for (int j = s; j < nb && j < s + NS; ++j) {
-            const uint32_t g2 = gcount + j;
-            mbar_wait(&mbar[g2 % NS], (g2 / NS) & 1u, timeout_ns);
-          }
-        __syncthreads();
-        gcount += nb < s + NS ? nb : s + NS;
-        return false;
-      }
+      pb[warp * 32 + lane] = (a[0] + a[1]) + (a[2] + a[3]);
+      __syncthreads();
       // every warp forms the same y_K
-      CT v = t[32 * K + lane];
+      CT v = CT(0);
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v -= pb[w * 32 + lane];
-#pragma unroll
-      for (int j = NREG - 1; j > 0; --j) yr[j] = yr[j - 1];
-      yr[0] = v;
+      for (int w = 0; w < NW; ++w) v += pb[w * 32 + lane];
+      wy[(K & 7) * 32 + lane] = v;
+      wy[256 + (K & 7) * 32 + lane] = v;
       if (warp == 0) y[32 * K + lane] = v;
-      // every warp has read slab st before the barrier: refill it
-      if (tid == 0 && !direct && s + NS < nb) {
-        const int Kb = dir == 0 ? s + NS : nb - 1 - (s + NS);
-        tma_load_1d(ring + st * ring_stride, base + Kb * slab, bytes, &mbar[st]);
-      }
+      cur = cur + 1 == D ? 0 : cur + 1;
     }
-    if (!direct) gcount += nb;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();  // y complete before the next pass reads it
   }
-  return true;
 }
 
 // m steps of textbook CG on A_p d = r from d = 0 (all threads). A_p in ELL
@@ -921,25 +931,23 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 // the persistent RAS kernel
 // --------------------------------------------------------------------------
 
-constexpr int kBandStages = 8;  // ring capacity; Launch::nstages of them are used
 
 template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
-  // band: ring | y | t | partials ; cg: r p q d ; ilu: r z p q d ; staged cg: A_p | p
-  static __host__ __device__ size_t ring_stride(int Wmax) {
-    const size_t b = (size_t)Wmax * 32 * sizeof(T);
-    return ((b + 127) / 128) * 128 / sizeof(T);
-  }
+  // band: copy rings | y | partials | window rings ; cg: r p q d ; ilu: r z p q d ;
+  // staged cg: A_p | p
+  static __host__ __device__ int band_twm(int Wmax) { return band_cols_per_warp(Wmax, NT / 32); }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
     return ((size_t)npad_max + 31) / 32 * 32;
   }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
   static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax, int nstages) {
     if (KIND == kBand) {
-      size_t b = (size_t)nstages * ring_stride(Wmax) * sizeof(T);
-      b += 2 * ylen(Wmax, npad_max) * sizeof(CT);  // y (r / delta), t
-      b += 2 * NT * sizeof(CT);                     // partials, two buffers
+      size_t b = (size_t)(NT / 32) * nstages * band_twm(Wmax) * 32 * sizeof(T);  // copy rings
+      b += ylen(Wmax, npad_max) * sizeof(CT);     // y (r / delta)
+      b += 2 * NT * sizeof(CT);                   // partials, two buffers
+      b += (size_t)(NT / 32) * 512 * sizeof(CT);  // per-warp window rings (two copies)
       return b;
     }
     if (KIND == kCGS) {
@@ -967,7 +975,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   __shared__ double s_red[NT / 32 * 2];
   __shared__ __align__(16) CT s_redc[2 * (NT / 32)];
   __shared__ int s_flag[8];
-  __shared__ __align__(8) uint64_t s_mbar[kBandStages];
+  __shared__ __align__(8) uint64_t s_mbar[1];
   __shared__ int s_done[kMaxCtaSys];
   __shared__ int64_t s_iter0[kMaxCtaSys];
 
@@ -979,15 +987,14 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
 
   // shared-memory carve-up
   T *ring = nullptr;
-  CT *ybuf = nullptr, *tbuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
-     *v4 = nullptr;
-  int ring_stride = 0;
+  CT *ybuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
+     *v4 = nullptr, *wbuf = nullptr;
+  const int twm = SM::band_twm(L.Wmax);
   if (KIND == kBand) {
-    ring_stride = (int)SM::ring_stride(L.Wmax);
     ring = reinterpret_cast<T *>(smem);
-    ybuf = reinterpret_cast<CT *>(smem + (size_t)L.nstages * ring_stride * sizeof(T));
-    tbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
-    pbuf = tbuf + SM::ylen(L.Wmax, L.npad_max);
+    ybuf = reinterpret_cast<CT *>(smem + (size_t)(NT / 32) * L.nstages * twm * 32 * sizeof(T));
+    pbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
+    wbuf = pbuf + 2 * NT;
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
     v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
@@ -1001,9 +1008,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     v4 = KIND == kILU ? base + 4 * vl : nullptr;
   }
   uint32_t gcount = 0;
-  if (KIND == kBand || KIND == kCGS) {
+  if (KIND == kCGS) {
     if (tid == 0) {
-      for (int s = 0; s < L.nstages; ++s) mbar_init(&s_mbar[s], 1);
+      mbar_init(&s_mbar[0], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
@@ -1054,16 +1061,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kBand) {
       __syncthreads();
       const T *fac = reinterpret_cast<const T *>(S.fac);
-      const int64_t slab = (int64_t)32 * D.W;
+      const int64_t rec = (int64_t)32 * (D.W + 32);
       const int nb = D.npad / 32;
       const T *F = fac + D.fac_off;
-      const bool ok = band_solve_m<T, CT, NT>(F, F + nb * slab, F + 2 * nb * slab, nb, D.W, ybuf,
-                                              tbuf, pbuf, ring, ring_stride, s_mbar, gcount,
-                                              L.timeout_ns, L.nstages, L.band_direct != 0);
-      if (!ok) {
-        if (tid == 0) set_error(L.ctl, kETIMEOUT, 2);
-        return false;
-      }
+      if (L.nstages >= 6)
+        band_solve_chain<T, CT, NT, 6>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
+      else
+        band_solve_chain<T, CT, NT, 4>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
     } else if (KIND == kCGS) {
       if (tid == 0) {
         const bool ok = mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);
@@ -1397,9 +1401,9 @@ static int occupancy_t(size_t smem) {
 #define RAS_DISPATCH(KIND_, PREC_, NT_, CALL)                                              \
   do {                                                                                     \
     if (KIND_ == kBand) {                                                                  \
-      if (PREC_ == kF64) { CALL(kBand, double, 256); }                                     \
-      else if (PREC_ == kF32) { CALL(kBand, float, 256); }                                 \
-      else { CALL(kBand, __nv_bfloat16, 256); }                                            \
+      if (PREC_ == kF64) { if (NT_ == 256) { CALL(kBand, double, 256); } else { CALL(kBand, double, 128); } } \
+      else if (PREC_ == kF32) { if (NT_ == 256) { CALL(kBand, float, 256); } else { CALL(kBand, float, 128); } } \
+      else { if (NT_ == 256) { CALL(kBand, __nv_bfloat16, 256); } else { CALL(kBand, __nv_bfloat16, 128); } } \
     } else if (KIND_ == kCGS) {                                                            \
       CALL(kCGS, float, 512);                                                              \
     } else if (KIND_ == kCG) {                                                             \
@@ -1420,8 +1424,8 @@ size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int k
 }
 
 int main_threads(int kind, int nt_pref) {
-  if (kind == kBand) return 256;
   if (kind == kCGS) return 512;
+  if (kind == kBand) return nt_pref == 128 ? 128 : 256;
   return nt_pref == 512 ? 512 : 256;
 }
 
