@@ -855,34 +855,34 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
                                             double &a_loc, double &a_own) {
   const int64_t eb = D.row_off * K;
   if constexpr (KC > 0) {
-    for (int i0 = threadIdx.x; i0 < D.npad; i0 += 2 * NT) {
-      int cols[2][KC], g[2];
-      double vals[2][KC], xs[2][KC], bb[2];
-      bool live[2], own[2];
+    // R rows per thread and pass: the index loads of all R rows are issued
+    // before the dependent loads of x and b, so that 2 R K loads are in flight
+    constexpr int R = 3;
+    for (int i0 = threadIdx.x; i0 < D.npad; i0 += R * NT) {
+      int cols[R][KC], g[R];
+      bool live[R], own[R];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < R; ++h) {
         const int i = i0 + h * NT;
         live[h] = i < D.n;
         const int ii = live[h] ? i : 0;
         g[h] = S.gidx[D.row_off + ii];
         own[h] = live[h] && S.ownf[D.row_off + ii];
 #pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          const int64_t e = eb + (int64_t)k * D.npad + ii;
-          cols[h][k] = S.rcol[e];
-          vals[h][k] = S.rval[e];
-        }
+        for (int k = 0; k < KC; ++k) cols[h][k] = S.rcol[eb + (int64_t)k * D.npad + ii];
       }
+      double xs[R][KC], bb[R];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        bb[h] = S.b[g[h]];
+      for (int h = 0; h < R; ++h) {
 #pragma unroll
         for (int k = 0; k < KC; ++k)
           xs[h][k] = async ? ld_relaxed_f64(xcur + cols[h][k]) : __ldcg(xcur + cols[h][k]);
+        bb[h] = S.b[g[h]];
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < R; ++h) {
         const int i = i0 + h * NT;
+        const int ii = live[h] ? i : 0;
         if (i >= D.npad) continue;
         double r = 0.0;
         if (live[h]) {
@@ -890,7 +890,7 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
           double xd = 0.0;
 #pragma unroll
           for (int k = 0; k < KC; ++k) {
-            r -= vals[h][k] * xs[h][k];
+            r -= S.rval[eb + (int64_t)k * D.npad + ii] * xs[h][k];
             xd = cols[h][k] == g[h] ? xs[h][k] : xd;
           }
           if (own[h]) {
