@@ -40,7 +40,8 @@ typedef enum {
   RAS_OK = 0,
   RAS_EINVAL = 1,   /* invalid argument (sizes, indices, pointers, options) */
   RAS_ENOMEM = 2,   /* host or device allocation failed */
-  RAS_ENOTSPD = 3,  /* a local factorisation met a non-positive pivot */
+  RAS_ENOTSPD = 3,  /* a local factorisation met a non-positive pivot, or a row of A_p
+                       has no positive diagonal entry (local CG) */
   RAS_ENOCONV = 4,  /* max updates / restarts reached; x holds the last iterate */
   RAS_ETIMEOUT = 5, /* a device-side wait exceeded its limit; x is undefined */
   RAS_ECUDA = 6,    /* a CUDA runtime call failed */

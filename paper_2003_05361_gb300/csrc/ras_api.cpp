@@ -819,6 +819,28 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     }
   });
   if (ilu_fail) return RAS_ENOTSPD;
+  // local CG: every ELL row starts with its diagonal (the staged kernel reuses
+  // p[i]); an SPD A_p has a positive diagonal in every row
+  if (kind == RAS_LOCAL_CG) {
+    std::atomic<int> nodiag(0);
+    parallel_for(P, [&](int p) {
+      const SubDesc &d = c->subs[p];
+      for (int i = 0; i < d.n; ++i) {
+        const int64_t e0 = d.row_off * K + i;
+        bool found = false;
+        for (int kl = 0; kl < K && !found; ++kl) {
+          const int64_t e = e0 + (int64_t)kl * d.npad;
+          if (lcol[e] == i && lval64[e] > 0.0) {
+            std::swap(lcol[e], lcol[e0]);
+            std::swap(lval64[e], lval64[e0]);
+            found = true;
+          }
+        }
+        if (!found) nodiag = 1;
+      }
+    });
+    if (nodiag) return RAS_ENOTSPD;
+  }
   std::vector<int32_t> levp_all, levr_all;
   if (kind == RAS_LOCAL_ILU0_CG) {
     for (int p = 0; p < P; ++p) {
@@ -935,6 +957,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       std::vector<int16_t> l16(lc.begin(), lc.end());
       if ((st = c->upload(c->d_lcol16, l16)) != RAS_OK) return st;
     }
+
     auto up_prec = [&](void *&dst, const std::vector<double> &src) -> ras_status {
       const size_t bytes = std::max<size_t>(src.size(), 1) * prec_bytes(prec);
       std::vector<unsigned char> tmp(bytes);

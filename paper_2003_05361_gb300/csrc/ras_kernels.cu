@@ -685,11 +685,14 @@ __device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad,
   }
 }
 
-// m steps of textbook CG with A_p staged in shared memory (FP32 values,
-// int16 local columns) and the vectors r, d, q in registers: thread t owns
-// rows t, t + NT, t + 2 NT, ... Only p lives in shared memory. On entry p
-// holds r (zero beyond n); on exit it holds d. KC > 0 is the ELL width known
-// at compile time (KC = 0: runtime K). red holds 2 * NT/32 floats.
+// m steps of textbook CG with A_p staged in shared memory (FP32 values, int16
+// local columns) and the vectors r, d, q in registers: thread t owns rows t,
+// t + NT, t + 2 NT, ... Only p lives in shared memory. Entry 0 of every row is
+// its diagonal, so p[i] is read once per step and reused for the diagonal
+// product, (p, q) and the updates; d += alpha p is applied together with the
+// p update (the same values as in the textbook order). On entry p holds r
+// (zero beyond n); on exit it holds d. KC > 0 is the ELL width known at
+// compile time (KC = 0: runtime K). red holds 2 * NT/32 floats.
 template <int NT, int RMAX, int KC>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
                                 int m, float *p, float *red) {
@@ -713,15 +716,16 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
       if (i < n) {
-        float s = 0.f;
+        const float pi = p[i];
+        float s = sval[i] * pi;
         if constexpr (KC > 0) {
 #pragma unroll
-          for (int e = 0; e < KC; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+          for (int e = 1; e < KC; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
         } else {
-          for (int e = 0; e < K; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+          for (int e = 1; e < K; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
         }
         q[k] = s;
-        pq += p[i] * s;
+        pq += pi * s;
       }
     }
     pq = block_sum_1b<NT, float>(pq, red1);
@@ -731,7 +735,6 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
       if (i < n) {
-        d[k] += alpha * p[i];
         r[k] -= alpha * q[k];
         rn += r[k] * r[k];
       }
@@ -742,7 +745,11 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
-      if (i < n) p[i] = r[k] + beta * p[i];
+      if (i < n) {
+        const float pi = p[i];
+        d[k] += alpha * pi;
+        p[i] = r[k] + beta * pi;
+      }
     }
     __syncthreads();
   }
@@ -855,21 +862,30 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
                                             double &a_loc, double &a_own) {
   const int64_t eb = D.row_off * K;
   if constexpr (KC > 0) {
+    // the descriptors live in shared memory: keep what the loop needs in
+    // registers (the stores below would otherwise force reloads)
+    const int n = D.n, npad = D.npad;
+    const int32_t *__restrict__ gidx = S.gidx + D.row_off;
+    const uint8_t *__restrict__ ownf = S.ownf + D.row_off;
+    const int32_t *__restrict__ rcol = S.rcol + eb;
+    const double *__restrict__ rval = S.rval + eb;
+    const double *__restrict__ bg = S.b;
+    double *__restrict__ xg = S.xg + D.row_off;
     // R rows per thread and pass: the index loads of all R rows are issued
     // before the dependent loads of x and b, so that 2 R K loads are in flight
     constexpr int R = 3;
-    for (int i0 = threadIdx.x; i0 < D.npad; i0 += R * NT) {
+    for (int i0 = threadIdx.x; i0 < npad; i0 += R * NT) {
       int cols[R][KC], g[R];
       bool live[R], own[R];
 #pragma unroll
       for (int h = 0; h < R; ++h) {
         const int i = i0 + h * NT;
-        live[h] = i < D.n;
+        live[h] = i < n;
         const int ii = live[h] ? i : 0;
-        g[h] = S.gidx[D.row_off + ii];
-        own[h] = live[h] && S.ownf[D.row_off + ii];
+        g[h] = gidx[ii];
+        own[h] = live[h] && ownf[ii];
 #pragma unroll
-        for (int k = 0; k < KC; ++k) cols[h][k] = S.rcol[eb + (int64_t)k * D.npad + ii];
+        for (int k = 0; k < KC; ++k) cols[h][k] = rcol[(int64_t)k * npad + ii];
       }
       double xs[R][KC], bb[R];
 #pragma unroll
@@ -877,24 +893,24 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 #pragma unroll
         for (int k = 0; k < KC; ++k)
           xs[h][k] = async ? ld_relaxed_f64(xcur + cols[h][k]) : __ldcg(xcur + cols[h][k]);
-        bb[h] = S.b[g[h]];
+        bb[h] = bg[g[h]];
       }
 #pragma unroll
       for (int h = 0; h < R; ++h) {
         const int i = i0 + h * NT;
         const int ii = live[h] ? i : 0;
-        if (i >= D.npad) continue;
+        if (i >= npad) continue;
         double r = 0.0;
         if (live[h]) {
           r = bb[h];
           double xd = 0.0;
 #pragma unroll
           for (int k = 0; k < KC; ++k) {
-            r -= S.rval[eb + (int64_t)k * D.npad + ii] * xs[h][k];
+            r -= rval[(int64_t)k * npad + ii] * xs[h][k];
             xd = cols[h][k] == g[h] ? xs[h][k] : xd;
           }
           if (own[h]) {
-            S.xg[D.row_off + i] = xd;
+            xg[i] = xd;
             a_own += r * r;
           }
           a_loc += r * r;
@@ -936,7 +952,7 @@ template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
   // band: copy rings | y | partials | window rings ; cg: r p q d ; ilu: r z p q d ;
-  // staged cg: A_p | p
+  // staged cg: A_p values | A_p columns | p
   static __host__ __device__ int band_twm(int Wmax) { return band_cols_per_warp(Wmax, NT / 32); }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
     return ((size_t)npad_max + 31) / 32 * 32;
