@@ -200,6 +200,12 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
         res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
         if kind == ras.RAS_LOCAL_CG:
             loc = nnz_p * (prec_bytes + 2) * (1 if staged else m)
+        elif kind == ras.RAS_LOCAL_BANDCHOL:
+            # local half-bandwidth of A_p in ascending global order
+            loc_col = np.searchsorted(om, ci[idx])
+            loc_row = np.repeat(np.arange(n_p), ends - starts)
+            w_p = int(np.max(np.where(inside[ci[idx]], loc_row - loc_col, 0)))
+            loc = 2 * n_p * (w_p + 1) * prec_bytes
         else:
             loc = 0
         out.append(res + loc + 8 * o_p)
@@ -353,6 +359,10 @@ def run_ours(args):
             "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 
+    band4 = None
+    if not args.quick and world == 1:
+        band4 = band_config4(dev, stream, args.band_iters)
+
     launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)
     line = {
         "metric": METRIC, "value": med, "unit": "ms", "n_gpus": world, "steps": args.steps,
@@ -370,6 +380,8 @@ def run_ours(args):
         "gpu_launches": launches_per_solve * args.steps,
         "roofline": roof, "clocks": clocks.summary(),
     }
+    if band4 is not None:
+        line["band_config4"] = band4
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
@@ -391,16 +403,73 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_profile_case(args):
-    """Small cases for ncu, each launch capped at `--profile-updates` local
-    updates per subdomain (a few ms):
-      cg_cfg2   the benchmark workload, async, FP32 local CG-20 (default);
-      band_cfg1 2D Poisson 128^2, 2x2, overlap 2, banded Cholesky FP32, sync."""
+def band_config4(dev, stream, iters: int):
+    """Kernel-level roofline of the banded-Cholesky path on the config-4
+    workload: 2D variable-coefficient diffusion 2048^2 (k = exp(GRF), sigma 1,
+    correlation length 1/32, seed 4), b uniform seed 4, regular 32x32 = 1024
+    subdomains, overlap 4; `iters` synchronous iterations (capped solve) with
+    factors stored in FP32 and in BF16, each timed with CUDA events inside the
+    library. Algorithmic bytes per update: residual rows + band model
+    2 n_p (w_p + 1) s_f + owned-row writes."""
     import torch
 
     import paper_2003_05361_gb300 as ras
 
-    if args.case == "band_cfg1":
+    n = 2048
+    A = problems.diffusion2d(n, problems.grf_coefficient(n, 4))
+    b = problems.rhs_uniform(A.n, 4)
+    part = ras.ras_partition_regular2d(n, n, 32, 32)
+    bd = torch.tensor(b, device=dev)
+    peak, peak_src = measured_peaks()
+    out = {"workload": "2D diffusion 2048x2048 (4,194,304 unknowns), k = exp(GRF sigma 1, "
+                       "ell 1/32, seed 4), regular2d 32x32 = 1024 subdomains, overlap 4, "
+                       f"banded Cholesky, sync, {iters} iterations per timed launch"}
+    for name, prec, sb in (("fp32", ras.RAS_FP32, 4), ("bf16", ras.RAS_BF16_STORE, 2)):
+        ctx = ras.ras_setup(A, part, 1024, 4, ras.RAS_LOCAL_BANDCHOL, prec, stream=stream)
+        per_upd = subdomain_bytes(A, ras, ctx, ras.RAS_LOCAL_BANDCHOL, sb, 1, True)
+        ms = []
+        for _ in range(3):
+            x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+            info = ras.ras_solve(ctx, bd, x, 1e-8, ras.RAS_SYNC, iters)
+            ms.append(info.kernel_ms)
+        counts = ras.ras_get_update_counts(ctx)
+        alg = float(np.dot(counts, per_upd))
+        k_ms = statistics.median(ms)
+        achieved = alg / (k_ms / 1e3) / 1e9
+        launch = ras.ras_get_launch(ctx)
+        tpu = profile_traffic(f"sync_band_{name}_cfg4")
+        out[name] = {"ms_per_iteration": k_ms / iters, "kernel_ms": k_ms,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "peak_source": peak_src,
+                                  "traffic": (tpu * float(counts.sum())) if tpu else None,
+                                  "algorithmic_bytes": alg,
+                                  "kernel": f"ras_main_kernel<band, {name}, {launch['cta_threads']}>",
+                                  "grid": launch["grid"]}}
+        ras.ras_destroy(ctx)
+    return out
+
+
+def run_profile_case(args):
+    """Small cases for ncu, each launch capped at `--profile-updates` local
+    updates per subdomain (a few ms):
+      cg_cfg2   the benchmark workload, async, FP32 local CG-20 (default);
+      band_cfg1 2D Poisson 128^2, 2x2, overlap 2, banded Cholesky FP32, sync;
+      band_cfg4s the config-4 subdomain shape on a quarter of the grid: 2D
+                diffusion 1024^2 (k = exp(GRF), seed 4), 16x16 = 256 subdomains
+                of 64x64, overlap 4, banded Cholesky FP32, sync (1.1 GB of
+                factor records, well over L2); its DRAM bytes per update stand
+                for the full config-4 launch."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    if args.case == "band_cfg4s":
+        A = problems.diffusion2d(1024, problems.grf_coefficient(1024, 4))
+        b = problems.rhs_uniform(A.n, 4)
+        part = ras.ras_partition_regular2d(1024, 1024, 16, 16)
+        ctx = ras.ras_setup(A, part, 256, 4, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP32)
+        mode, variant = ras.RAS_SYNC, "sync_band_fp32_cfg4"
+    elif args.case == "band_cfg1":
         A = problems.poisson2d(128)
         b, _, _ = problems.rhs_eigen2d(128)
         part = ras.ras_partition_regular2d(128, 128, 2, 2)
@@ -461,7 +530,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--profile", action="store_true", help="run the small ncu case only")
     ap.add_argument("--profile-updates", type=int, default=20)
-    ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1"])
+    ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1", "band_cfg4s"])
+    ap.add_argument("--band-iters", type=int, default=200,
+                    help="sync iterations of the config-4 band roofline launch")
     ap.add_argument("--serve", action="store_true", help="run the serving workload only")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=20.0)
