@@ -507,7 +507,7 @@ def run_serving(args):
     for name, mode, prec in (("async_fp32", ras.RAS_ASYNC, ras.RAS_FP32),
                              ("sync_fp64", ras.RAS_SYNC, ras.RAS_FP64)):
         reqs = request_stream(args.serve_requests, rate=args.serve_rate, seed=5)
-        srv = Server(mode=mode, prec=prec, step_limit=args.serve_step)
+        srv = Server(mode=mode, prec=prec, step_limit=args.serve_step, workers=args.serve_workers)
         stats = srv.run(reqs)
         out[name] = stats
         print(json.dumps({"serving": name, **stats}), flush=True)
@@ -515,7 +515,8 @@ def run_serving(args):
             "unit": "ms", "value": out["async_fp32"].get("p99_ms"), "higher_is_better": False,
             "config": {"workload": f"{args.serve_requests} seeded Poisson-arrival 2D Poisson solves, "
                                    f"side U{{64..512}}, rate {args.serve_rate}/s, 64x64 subdomains, "
-                                   "overlap 2, banded Cholesky, tol 1e-8"},
+                                   "overlap 2, banded Cholesky, tol 1e-8",
+                       "setup_workers": args.serve_workers},
             "variants": out}
     print(json.dumps(line), flush=True)
 
@@ -537,6 +538,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-step", type=int, default=20)
+    ap.add_argument("--serve-workers", type=int, default=2, help="host threads doing request setup")
     args = ap.parse_args()
     if args.serve:
         run_serving(args)

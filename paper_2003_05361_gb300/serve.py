@@ -203,6 +203,9 @@ class Server:
 
         first = min(r.arrival for r in self.records)
         last = max(r.finished for r in self.records)
+        wait = [r.admitted - r.arrival for r in self.records]
+        setup = [r.started - r.admitted for r in self.records]
+        run = [r.finished - r.started for r in self.records]
         return {
             "completed": len(lat),
             "failed": sum(1 for r in self.records if r.status != 0),
@@ -213,4 +216,9 @@ class Server:
             "wall_s": wall,
             "steps": steps,
             "max_relres": max(r.relres for r in self.records),
+            # where a request's latency goes: waiting for admission, host and
+            # device setup (maps, factorisation), and solving in the batch
+            "admission_wait_ms_mean": 1e3 * statistics.fmean(wait),
+            "setup_ms_mean": 1e3 * statistics.fmean(setup),
+            "solve_ms_mean": 1e3 * statistics.fmean(run),
         }
