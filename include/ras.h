@@ -48,7 +48,15 @@ typedef enum {
   RAS_ENOTSUP = 7   /* valid but unsupported (e.g. local bandwidth too large) */
 } ras_status;
 
-typedef enum { RAS_SYNC = 0, RAS_ASYNC = 1 } ras_mode;
+/* RAS_SYNC: iterations separated by a grid-wide barrier. RAS_ASYNC: no
+ * barrier; a subdomain stops when a device counter of locally converged
+ * subdomains (Eq. 2) reaches P (the one-GPU form of the centralized detection
+ * of Sec. 3.3.2). RAS_ASYNC_DECENTRAL: no barrier; decentralized, leader-based
+ * detection (Sec. 3.3.2): a locally converged subdomain whose neighbours all
+ * report local convergence raises a global flag, which every subdomain that
+ * sees it on a neighbour raises too before it stops. Both asynchronous modes
+ * then verify the global criterion on the frozen x and resume if it fails. */
+typedef enum { RAS_SYNC = 0, RAS_ASYNC = 1, RAS_ASYNC_DECENTRAL = 2 } ras_mode;
 
 /* Local solvers (Sec. 3.3.1): a banded Cholesky factorisation computed once
  * in ras_setup with triangular solves in every update, or `inner_iters` steps

@@ -484,7 +484,15 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   int64_t cap = (int64_t)occ * nsm;
   const int64_t lim = env_int("RAS_MAX_CTAS", 0);
   if (lim > 0) cap = std::min<int64_t>(cap, lim);
-  pl.grid = (int)std::min<int64_t>((int64_t)items.size(), cap);
+  // as many CTAs as give every CTA the same number of subdomains (the most
+  // any CTA would get anyway): a synchronous iteration takes as long as its
+  // fullest CTA either way, and in the asynchronous mode subdomains then
+  // update at the same rate (unequal counts, e.g. 256 subdomains on 152 CTAs,
+  // made some update twice as often as their neighbours, and the iteration
+  // with CG-20 local solves then often failed to converge)
+  const int64_t nit = (int64_t)items.size();
+  const int64_t per = (nit + cap - 1) / std::max<int64_t>(cap, 1);
+  pl.grid = (int)(per > 0 ? (nit + per - 1) / per : 0);
   if (pl.grid <= 0) return RAS_EINVAL;
   assign_items(pl, items, cost, pl.grid);
   auto up = [&](auto *&d, const auto &v) -> cudaError_t {
@@ -1012,6 +1020,7 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.timeout_ns = timeout_ns();
   L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
   L.max_restarts = 8;
+  L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
   L.m = m;
   L.Wmax = pl.Wmax;
   L.npad_max = pl.npad_max;
@@ -1071,7 +1080,7 @@ ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const
 
 ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t mode,
                      int64_t max_updates, ras_solve_info *info) {
-  if (!c || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC)) return RAS_EINVAL;
+  if (!c || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC && mode != RAS_ASYNC_DECENTRAL)) return RAS_EINVAL;
   if (info) std::memset(info, 0, sizeof(*info));
   *c->h_sysdesc = make_sysdesc(c, b, x, tol);
   CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
@@ -1111,7 +1120,7 @@ ras_status ras_solve_host(ras_ctx *c, const double *b_host, double *x_host, doub
 ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *const *b,
                            double *const *x, double tol, int32_t mode, int64_t max_updates,
                            ras_solve_info *infos) {
-  if (!ctxs || num <= 0 || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC))
+  if (!ctxs || num <= 0 || !b || !x || !(tol > 0.0) || (mode != RAS_SYNC && mode != RAS_ASYNC && mode != RAS_ASYNC_DECENTRAL))
     return RAS_EINVAL;
   for (int s = 0; s < num; ++s)
     if (!ctxs[s] || !b[s] || !x[s] || ctxs[s]->exec_kind != ctxs[0]->exec_kind ||
@@ -1250,7 +1259,7 @@ thread_local StepCache g_step;
 
 ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64_t step_limit,
                           int64_t max_updates, int32_t *done, ras_solve_info *infos) {
-  if (!ctxs || num <= 0 || step_limit <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
+  if (!ctxs || num <= 0 || step_limit <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC && mode != RAS_ASYNC_DECENTRAL))
     return RAS_EINVAL;
   for (int s = 0; s < num; ++s) {
     if (!ctxs[s] || !ctxs[s]->begun || ctxs[s]->exec_kind != ctxs[0]->exec_kind ||
@@ -1316,6 +1325,7 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   L.timeout_ns = timeout_ns();
   L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
   L.max_restarts = 8;
+  L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
   L.m = c0->ls.inner_iters;
   L.Wmax = sc.plan.Wmax;
   L.npad_max = sc.plan.npad_max;
@@ -1401,7 +1411,7 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
 
 ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t iters,
                         int32_t tune_inner, ras_tune_result *out) {
-  if (!c || !x_scratch || iters <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC))
+  if (!c || !x_scratch || iters <= 0 || (mode != RAS_SYNC && mode != RAS_ASYNC && mode != RAS_ASYNC_DECENTRAL))
     return RAS_EINVAL;
   // homogeneous problem A x = 0 from x = 1: the error is x itself, dominated
   // by the smoothest modes, so a short window sees the asymptotic rate

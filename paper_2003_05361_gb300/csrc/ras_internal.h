@@ -21,7 +21,7 @@ namespace ras {
 enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2,
                           kCGS = 3 };  // kCGS: CG with A_p staged in shared memory (kernel variant)
 enum Prec : int32_t { kF64 = 0, kF32 = 1, kBF16 = 2 };
-enum Mode : int32_t { kSync = 0, kAsync = 1 };
+enum Mode : int32_t { kSync = 0, kAsync = 1, kAsyncDecentral = 2 };
 // status codes (mirror ras_status)
 enum : int32_t { kOK = 0, kEINVAL = 1, kENOMEM = 2, kENOTSPD = 3, kENOCONV = 4, kETIMEOUT = 5,
                  kECUDA = 6, kENOTSUP = 7 };
@@ -59,6 +59,8 @@ struct SubState {
   int32_t conv_epoch; // async: epoch in which Eq. 2 last held (-1: not converged)
   int32_t park_epoch;
   int32_t check_epoch;
+  int32_t gconv_epoch;  // decentralized detection: epoch of the global flag (-1: none)
+  int32_t pad_;
 };
 
 struct SysState {
@@ -144,7 +146,7 @@ struct Launch {
   int32_t persist;             // async: keep polling until every system is done
   int32_t kmax;                // largest ELL width over the launch
   int32_t nstages;             // band: slab ring depth (2..8)
-  int32_t pad2_;
+  int32_t fresh;               // async: update only after a neighbour published since the last update
 };
 
 }  // namespace ras

@@ -48,8 +48,21 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_s32(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
   int v;
@@ -449,6 +462,7 @@ __global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
     s.conv_epoch = -1;
     s.park_epoch = -1;
     s.check_epoch = -1;
+    s.gconv_epoch = -1;
   }
 }
 
@@ -1037,7 +1051,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   }
   __syncthreads();
 
-  const bool async = L.mode == kAsync;
+  const bool async = L.mode != kSync;
+  const bool decentral = L.mode == kAsyncDecentral;
   // wall-clock limit of the whole solve (each CTA measures from its own start)
   const uint64_t t_start = gtimer();
   auto past_deadline = [&]() -> bool {
@@ -1241,11 +1256,34 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
           else if (phase != kDone) {
             s_flag[3] = 0;
             if (phase == kRun) {
-              if (ss.updates >= L.max_updates) {
+              // decentralized detection: the global flag, raised here or seen
+              // on a neighbour, stops this subdomain (it parks)
+              bool flag = false;
+              if (decentral) {
+                flag = ld_relaxed_s32(&ss.gconv_epoch) == epoch;
+                if (!flag) {
+                  const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+                  for (int q = 0; q < s_sub.n_nbr && !flag; ++q)
+                    flag = ld_acquire_s32(&s_sys.sub[nb[q]].gconv_epoch) == epoch;
+                  if (flag) st_release_s32(&ss.gconv_epoch, epoch);
+                }
+              }
+              if (flag) {
+                if (ss.park_epoch != epoch) action = 2;
+              } else if (ss.updates >= L.max_updates) {
                 st->status = kENOCONV;
                 atomicCAS(&st->word, wd, ((uint32_t)epoch << 2) | kDone);
               } else if (ss.step_updates < L.step_limit) {
                 action = 1;
+                if (L.fresh && ss.updates > 0 && s_sub.n_nbr > 0) {
+                  // wait for new neighbour data instead of repeating the solve
+                  // on the same interface values
+                  uint64_t seen = 0;
+                  const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+                  for (int q = 0; q < s_sub.n_nbr; ++q)
+                    seen += ld_relaxed_u32(&s_sys.sub[nb[q]].version);
+                  if (seen == ss.nbr_seen) action = 0;
+                }
               }
             } else if (phase == kDrain) {
               if (ss.park_epoch != epoch) action = 2;
@@ -1284,7 +1322,18 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
             st_release_u32(&ss.version, (uint32_t)ss.updates);
             // local criterion (Eq. 2) on the residual gathered before the update
             const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
-            if (conv && ss.conv_epoch != epoch) {
+            if (decentral) {
+              // publish the local status; a converged subdomain whose
+              // neighbours all report local convergence raises the global flag
+              st_release_s32(&ss.conv_epoch, conv ? epoch : -1);
+              if (conv) {
+                bool all = true;
+                const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+                for (int q = 0; q < s_sub.n_nbr && all; ++q)
+                  all = ld_acquire_s32(&s_sys.sub[nb[q]].conv_epoch) == epoch;
+                if (all) st_release_s32(&ss.gconv_epoch, epoch);
+              }
+            } else if (conv && ss.conv_epoch != epoch) {
               ss.conv_epoch = epoch;
               const int nc = atomicAdd(&st->nconv, 1) + 1;
               if (nc == s_sys.P) atomicCAS(&st->word, ((uint32_t)epoch << 2) | kRun,
