@@ -1019,7 +1019,9 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.step_limit = (int64_t)1 << 62;
   L.timeout_ns = timeout_ns();
   L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
-  L.max_restarts = 8;
+  // the leader-based scheme stops on any fully converged neighbourhood, so a
+  // failed global check is routine there: it resumes until max_updates
+  L.max_restarts = mode == RAS_ASYNC_DECENTRAL ? (1 << 30) : 8;
   L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
   L.m = m;
   L.Wmax = pl.Wmax;
@@ -1324,7 +1326,9 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   L.step_limit = step_limit;
   L.timeout_ns = timeout_ns();
   L.solve_limit_ns = env_int("RAS_SOLVE_LIMIT_MS", 120000) * 1000000ll;
-  L.max_restarts = 8;
+  // the leader-based scheme stops on any fully converged neighbourhood, so a
+  // failed global check is routine there: it resumes until max_updates
+  L.max_restarts = mode == RAS_ASYNC_DECENTRAL ? (1 << 30) : 8;
   L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
   L.m = c0->ls.inner_iters;
   L.Wmax = sc.plan.Wmax;
