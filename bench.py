@@ -462,6 +462,69 @@ def band_config4(dev, stream, iters: int):
     return out
 
 
+def run_sweep(args):
+    """One-GPU analogues of the paper's overlap and partitioning experiments
+    (Sec. 4.3-4.5) on the benchmark's 2D Poisson problem (1024^2, b seed 1) in
+    256 subdomains, regular2d 16x16 or seeded BFS growth (seed 1): overlap
+    1 / 2 / 4 / 8 with banded Cholesky local solves in FP32 (the paper's direct
+    local solver; BFS parts exceed its bandwidth limit) and overlap 1 / 2 / 4
+    with CG-20 in FP32, synchronous vs asynchronous; for overlap 4 with the
+    banded solver also the decentralized detection scheme (Sec. 3.3.2). One
+    solve per synchronous point, the median (by time) of 3 per asynchronous
+    point."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    torch.cuda.set_device(0)
+    A, b = problem()
+    bd = torch.tensor(b, device="cuda")
+    parts = {"regular2d": ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX),
+             "bfs": ras.ras_partition_bfs(A, PX * PX, 1)}
+    solvers = {"band_fp32": (ras.RAS_LOCAL_BANDCHOL, 1, (1, 2, 4, 8)),
+               "cg20_fp32": (ras.RAS_LOCAL_CG, M_INNER, (1, 2, 4))}
+    rows = []
+
+    def run(ctx, mode, reps):
+        out = []
+        for _ in range(reps):
+            x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+            out.append(ras.ras_solve(ctx, bd, x, TOL, mode))
+        out.sort(key=lambda i: i.kernel_ms)
+        return out[len(out) // 2]
+
+    for pname, part in parts.items():
+        for sname, (kind, m, gammas) in solvers.items():
+            for gamma in gammas:
+                try:
+                    ctx = ras.ras_setup(A, part, PX * PX, gamma, kind, ras.RAS_FP32, m)
+                except ras.RasError as err:
+                    row = {"partition": pname, "local": sname, "overlap": gamma, "error": str(err)}
+                    rows.append(row)
+                    print(json.dumps(row), flush=True)
+                    continue
+                modes = [("sync", ras.RAS_SYNC, 1), ("async", ras.RAS_ASYNC, 3)]
+                if gamma == 4 and kind == ras.RAS_LOCAL_BANDCHOL:
+                    modes.append(("async_decentral", ras.RAS_ASYNC_DECENTRAL, 3))
+                for mname, mode, reps in modes:
+                    info = run(ctx, mode, reps)
+                    ph = ras.ras_get_phase_times(ctx).astype(np.float64)
+                    upd = np.maximum(ras.ras_get_update_counts(ctx), 1).astype(np.float64)
+                    per = (ph / upd[:, None]).mean(0) / 1e3
+                    row = {"partition": pname, "local": sname, "overlap": gamma, "mode": mname,
+                           "status": info.status, "ms": info.kernel_ms,
+                           "iterations": info.iterations, "updates_min": info.updates_min,
+                           "updates_max": info.updates_max, "restarts": info.restarts,
+                           "relres": info.relres,
+                           "us_per_update": {"gather": per[0], "solve": per[1], "update": per[2]},
+                           "max_local_bandwidth": int(ras.ras_get_info(ctx)["max_bandwidth"])}
+                    rows.append(row)
+                    print(json.dumps(row), flush=True)
+                ras.ras_destroy(ctx)
+    print(json.dumps({"sweep": "partition x local solver x overlap x mode (2D Poisson 1024^2, "
+                               "256 subdomains, FP32 local solves)", "rows": rows}), flush=True)
+
+
 def run_profile_case(args):
     """Small cases for ncu, each launch capped at `--profile-updates` local
     updates per subdomain (a few ms):
@@ -547,13 +610,17 @@ def main():
     ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1", "band_cfg4s"])
     ap.add_argument("--band-iters", type=int, default=200,
                     help="sync iterations of the config-4 band roofline launch")
+    ap.add_argument("--sweep", action="store_true",
+                    help="overlap / partition / detection sweep on the benchmark problem")
     ap.add_argument("--serve", action="store_true", help="run the serving workload only")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-step", type=int, default=20)
     ap.add_argument("--serve-workers", type=int, default=2, help="host threads doing request setup")
     args = ap.parse_args()
-    if args.serve:
+    if args.sweep:
+        run_sweep(args)
+    elif args.serve:
         run_serving(args)
     elif args.profile:
         run_profile_case(args)
