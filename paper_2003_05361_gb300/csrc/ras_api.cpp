@@ -161,6 +161,7 @@ struct ras_ctx {
   SubState *d_sub = nullptr;
   SysState *d_st = nullptr;
   int16_t *d_lcol16 = nullptr;
+  int32_t *d_own_g = nullptr;
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
   uint8_t *d_ownf = nullptr;
@@ -525,6 +526,7 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.rcol = c->d_rcol;
   s.rval = c->d_rval;
   s.own_l = c->d_own;
+  s.own_g = c->d_own_g;
   s.xg = c->d_xg;
   s.fac = c->d_fac;
   s.lcol = c->d_lcol;
@@ -890,6 +892,14 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   if ((st = c->upload(c->d_rcol, rcol)) != RAS_OK) return st;
   if ((st = c->upload(c->d_rval, rval)) != RAS_OK) return st;
   if ((st = c->upload(c->d_own, own)) != RAS_OK) return st;
+  {
+    std::vector<int32_t> own_g(own.size());
+    for (int p = 0; p < P; ++p) {
+      const SubDesc &d = c->subs[p];
+      for (int t = 0; t < d.n_own; ++t) own_g[d.own_off + t] = gidx[d.row_off + own[d.own_off + t]];
+    }
+    if ((st = c->upload(c->d_own_g, own_g)) != RAS_OK) return st;
+  }
   if ((st = c->upload(c->d_nbr, nbr)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_xalt, n)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_xg, (size_t)rows)) != RAS_OK) return st;

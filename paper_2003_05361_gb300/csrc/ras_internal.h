@@ -94,6 +94,7 @@ struct SysDesc {
   const int32_t *rcol;
   const double *rval;
   const int32_t *own_l;
+  const int32_t *own_g;  // global index of each owned row (same order as own_l)
   double *xg;    // per local row: the x value the last gather used (owned rows)
   const void *fac;
   const int32_t *lcol;

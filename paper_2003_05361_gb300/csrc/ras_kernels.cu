@@ -886,8 +886,8 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
     const double *__restrict__ bg = S.b;
     double *__restrict__ xg = S.xg + D.row_off;
     // R rows per thread and pass: the index loads of all R rows are issued
-    // before the dependent loads of x and b, so that 2 R K loads are in flight
-    constexpr int R = 3;
+    // first, then x, b and the matrix values in one round of independent loads
+    constexpr int R = 2;
     for (int i0 = threadIdx.x; i0 < npad; i0 += R * NT) {
       int cols[R][KC], g[R];
       bool live[R], own[R];
@@ -901,18 +901,20 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 #pragma unroll
         for (int k = 0; k < KC; ++k) cols[h][k] = rcol[(int64_t)k * npad + ii];
       }
-      double xs[R][KC], bb[R];
+      double xs[R][KC], vs[R][KC], bb[R];
 #pragma unroll
       for (int h = 0; h < R; ++h) {
+        const int ii = live[h] ? i0 + h * NT : 0;
 #pragma unroll
-        for (int k = 0; k < KC; ++k)
+        for (int k = 0; k < KC; ++k) {
           xs[h][k] = async ? ld_relaxed_f64(xcur + cols[h][k]) : __ldcg(xcur + cols[h][k]);
+          vs[h][k] = rval[(int64_t)k * npad + ii];
+        }
         bb[h] = bg[g[h]];
       }
 #pragma unroll
       for (int h = 0; h < R; ++h) {
         const int i = i0 + h * NT;
-        const int ii = live[h] ? i : 0;
         if (i >= npad) continue;
         double r = 0.0;
         if (live[h]) {
@@ -920,7 +922,7 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
           double xd = 0.0;
 #pragma unroll
           for (int k = 0; k < KC; ++k) {
-            r -= rval[(int64_t)k * npad + ii] * xs[h][k];
+            r -= vs[h][k] * xs[h][k];
             xd = cols[h][k] == g[h] ? xs[h][k] : xd;
           }
           if (own[h]) {
@@ -1133,17 +1135,35 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       delta = v4;
     }
     if (tid == 0) t2 = gtimer();
-    // restricted prolongation: only owned rows are written (RAS)
-    const int32_t *own = S.own_l + D.own_off;
-    for (int t = tid; t < D.n_own; t += NT) {
-      const int i = own[t];
-      const int g = S.gidx[D.row_off + i];
-      // x_g + delta on an owned row is the owned part of the local solution
-      // computed from the very values this gather read, whatever other
-      // subdomains (or delays) did to x meanwhile
-      const double xn = S.xg[D.row_off + i] + (double)delta[i];
-      if (async) st_relaxed_f64(xnext + g, xn);
-      else __stcg(xnext + g, xn);
+    // restricted prolongation: only owned rows are written (RAS). x_g + delta
+    // on an owned row is the owned part of the local solution computed from
+    // the very values this gather read, whatever other subdomains (or delays)
+    // did to x meanwhile. Four rows per thread and pass, loads first.
+    {
+      const int32_t *__restrict__ own = S.own_l + D.own_off;
+      const int32_t *__restrict__ owng = S.own_g + D.own_off;
+      const double *__restrict__ xgl = S.xg + D.row_off;
+      const int no = D.n_own;
+      constexpr int U = 4;
+      for (int t0 = tid; t0 < no; t0 += U * NT) {
+        int li[U], gg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int t = t0 + u * NT;
+          li[u] = t < no ? own[t] : 0;
+          gg[u] = t < no ? owng[t] : 0;
+        }
+        double xn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) xn[u] = xgl[li[u]] + (double)delta[li[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (t0 + u * NT < no) {
+            if (async) st_relaxed_f64(xnext + gg[u], xn[u]);
+            else __stcg(xnext + gg[u], xn[u]);
+          }
+        }
+      }
     }
     __threadfence();
     __syncthreads();
