@@ -699,79 +699,111 @@ __device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad,
   }
 }
 
-// m steps of textbook CG with A_p staged in shared memory (FP32 values, int16
-// local columns) and the vectors r, d, q in registers: thread t owns rows t,
-// t + NT, t + 2 NT, ... Only p lives in shared memory. Entry 0 of every row is
-// its diagonal, so p[i] is read once per step and reused for the diagonal
-// product, (p, q) and the updates; d += alpha p is applied together with the
-// p update (the same values as in the textbook order). On entry p holds r
-// (zero beyond n); on exit it holds d. KC > 0 is the ELL width known at
-// compile time (KC = 0: runtime K). red holds 2 * NT/32 floats.
+// Two deterministic block sums with one barrier: callers alternate between
+// two buffers of 2 NT/32 values (see block_sum_1b).
+template <int NT>
+__device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = a;
+    red[NT / 32 + (threadIdx.x >> 5)] = b;
+  }
+  __syncthreads();
+  float sa = red[0], sb = red[NT / 32];
+#pragma unroll
+  for (int i = 1; i < NT / 32; ++i) {
+    sa += red[i];
+    sb += red[NT / 32 + i];
+  }
+  a = sa;
+  b = sb;
+}
+
+// m steps of CG on A_p d = r from d = 0 in the Chronopoulos-Gear
+// arrangement (the same iterates as textbook CG in exact arithmetic, one
+// synchronisation per step): with w = A r, gamma = (r, r), delta = (w, r),
+//   p = r + beta p, s = w + beta s, d += alpha p, r -= alpha s,
+//   w = A r, gamma' = (r, r), delta' = (w, r)   (one fused reduction),
+//   beta' = gamma'/gamma, alpha' = gamma' / (delta' - beta' gamma'/alpha).
+// A_p is staged in shared memory (FP32 values, int16 local columns, the
+// diagonal first in every row). r lives in shared memory (the operand of the
+// products, read once per step per row and reused); p, s, d, w live in
+// registers: thread t owns rows t, t + NT, ... On entry r holds the local
+// residual (zero beyond n); on exit it holds d. KC > 0 is the ELL width known
+// at compile time (KC = 0: runtime K). red holds 4 * NT/32 floats.
 template <int NT, int RMAX, int KC>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
-                                int m, float *p, float *red) {
+                                int m, float *r, float *red) {
   const int tid = threadIdx.x;
-  float *red0 = red, *red1 = red + NT / 32;
-  float r[RMAX], d[RMAX], q[RMAX];
-  float rr = 0.f;
-#pragma unroll
-  for (int k = 0; k < RMAX; ++k) {
-    const int i = tid + k * NT;
-    r[k] = i < n ? p[i] : 0.f;
-    d[k] = 0.f;
-    q[k] = 0.f;
-    rr += r[k] * r[k];
-  }
-  __syncthreads();  // red buffers free
-  rr = block_sum_1b<NT, float>(rr, red0);
-  for (int it = 0; it < m && rr != 0.f; ++it) {
-    float pq = 0.f;
+  float *red0 = red, *red1 = red + 2 * (NT / 32);
+  float p[RMAX], s[RMAX], d[RMAX], w[RMAX];
+  // w = A r and the two products of r
+  auto product = [&](float &gam, float &del) {
+    gam = 0.f;
+    del = 0.f;
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
+      float wi = 0.f;
       if (i < n) {
-        const float pi = p[i];
-        float s = sval[i] * pi;
+        const float ri = r[i];
+        wi = sval[i] * ri;
         if constexpr (KC > 0) {
 #pragma unroll
-          for (int e = 1; e < KC; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+          for (int e = 1; e < KC; ++e) wi += sval[e * npad + i] * r[scol[e * npad + i]];
         } else {
-          for (int e = 1; e < K; ++e) s += sval[e * npad + i] * p[scol[e * npad + i]];
+          for (int e = 1; e < K; ++e) wi += sval[e * npad + i] * r[scol[e * npad + i]];
         }
-        q[k] = s;
-        pq += pi * s;
+        gam += ri * ri;
+        del += wi * ri;
       }
+      w[k] = wi;
     }
-    pq = block_sum_1b<NT, float>(pq, red1);
-    const float alpha = rr / pq;
-    float rn = 0.f;
+  };
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    p[k] = 0.f;
+    s[k] = 0.f;
+    d[k] = 0.f;
+  }
+  __syncthreads();  // r complete, red buffers free
+  float gam, del;
+  product(gam, del);
+  block_sum2f_1b<NT>(gam, del, red0);
+  float alpha = gam != 0.f ? gam / del : 0.f, beta = 0.f;
+  int buf = 1;
+  for (int it = 0; it < m && gam != 0.f; ++it) {
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
       if (i < n) {
-        r[k] -= alpha * q[k];
-        rn += r[k] * r[k];
+        const float ri = r[i];
+        p[k] = ri + beta * p[k];
+        s[k] = w[k] + beta * s[k];
+        d[k] += alpha * p[k];
+        r[i] = ri - alpha * s[k];
       }
     }
-    rn = block_sum_1b<NT, float>(rn, red0);
-    const float beta = rn / rr;
-    rr = rn;
-#pragma unroll
-    for (int k = 0; k < RMAX; ++k) {
-      const int i = tid + k * NT;
-      if (i < n) {
-        const float pi = p[i];
-        d[k] += alpha * pi;
-        p[i] = r[k] + beta * pi;
-      }
-    }
-    __syncthreads();
+    __syncthreads();  // r complete before the product reads neighbours
+    if (it + 1 == m) break;
+    float g2, d2;
+    product(g2, d2);
+    block_sum2f_1b<NT>(g2, d2, buf ? red1 : red0);
+    buf ^= 1;
+    if (g2 == 0.f) break;
+    beta = g2 / gam;
+    alpha = g2 / (d2 - beta * g2 / alpha);
+    gam = g2;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < RMAX; ++k) {
     const int i = tid + k * NT;
-    if (i < npad) p[i] = i < n ? d[k] : 0.f;
+    if (i < npad) r[i] = i < n ? d[k] : 0.f;
   }
   __syncthreads();
 }
@@ -1005,7 +1037,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   __shared__ SysDesc s_sys;
   __shared__ SubDesc s_sub;
   __shared__ double s_red[NT / 32 * 2];
-  __shared__ __align__(16) CT s_redc[2 * (NT / 32)];
+  __shared__ __align__(16) CT s_redc[4 * (NT / 32)];
   __shared__ int s_flag[8];
   __shared__ __align__(8) uint64_t s_mbar[1];
   __shared__ int s_done[kMaxCtaSys];
