@@ -518,6 +518,13 @@ def run_sweep(args):
                            "relres": info.relres,
                            "us_per_update": {"gather": per[0], "solve": per[1], "update": per[2]},
                            "max_local_bandwidth": int(ras.ras_get_info(ctx)["max_bandwidth"])}
+                    if mode != ras.RAS_SYNC:
+                        # spread of the per-subdomain update counts (Figs. 6c / 7c)
+                        cnt = ras.ras_get_update_counts(ctx)
+                        hist, edges = np.histogram(cnt, bins=8)
+                        row["update_histogram"] = {"counts": hist.tolist(),
+                                                   "edges": [float(e) for e in edges]}
+                        row["stale_updates"] = info.stale_updates
                     rows.append(row)
                     print(json.dumps(row), flush=True)
                 ras.ras_destroy(ctx)
