@@ -161,6 +161,8 @@ struct ras_ctx {
   SubState *d_sub = nullptr;
   SysState *d_st = nullptr;
   int16_t *d_lcol16 = nullptr;
+  float *d_vpair = nullptr;     // staged CG, paired layout
+  uint32_t *d_cpair = nullptr;
   int32_t *d_own_g = nullptr;
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
@@ -531,6 +533,8 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.fac = c->d_fac;
   s.lcol = c->d_lcol;
   s.lcol16 = c->d_lcol16;
+  s.vpair = c->d_vpair;
+  s.cpair = c->d_cpair;
   s.lval = c->d_lval;
   s.luval = c->d_lu;
   s.lev_ptr = c->d_levp;
@@ -974,6 +978,27 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && npad_max <= kStagedRows) {
       std::vector<int16_t> l16(lc.begin(), lc.end());
       if ((st = c->upload(c->d_lcol16, l16)) != RAS_OK) return st;
+      if (K % 2 == 1 && K >= 3 && K <= 7) {
+        // paired layout for the staged kernel (diagonal first, then pairs)
+        std::vector<float> vp(lval64.size(), 0.f);
+        std::vector<uint32_t> cp(lval64.size() / 2 + 1, 0u);
+        for (int p = 0; p < P; ++p) {
+          const SubDesc &d = c->subs[p];
+          const int64_t eb = d.row_off * K, np = d.npad;
+          for (int i = 0; i < d.npad; ++i) {
+            vp[eb + i] = (float)lval64[eb + i];
+            for (int q = 0; q < (K - 1) / 2; ++q) {
+              const int64_t e1 = eb + (int64_t)(1 + 2 * q) * np + i, e2 = e1 + np;
+              vp[eb + np + 2 * ((int64_t)q * np + i)] = (float)lval64[e1];
+              vp[eb + np + 2 * ((int64_t)q * np + i) + 1] = (float)lval64[e2];
+              cp[eb / 2 + (int64_t)q * np + i] =
+                  (uint32_t)(uint16_t)lc[e1] | ((uint32_t)(uint16_t)lc[e2] << 16);
+            }
+          }
+        }
+        if ((st = c->upload(c->d_vpair, vp)) != RAS_OK) return st;
+        if ((st = c->upload(c->d_cpair, cp)) != RAS_OK) return st;
+      }
     }
 
     auto up_prec = [&](void *&dst, const std::vector<double> &src) -> ras_status {

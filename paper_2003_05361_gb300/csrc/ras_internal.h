@@ -99,6 +99,12 @@ struct SysDesc {
   const void *fac;
   const int32_t *lcol;
   const int16_t *lcol16;  // local columns as int16 (staged CG)
+  // staged CG, paired layout (odd ELL width K, diagonal first): per subdomain
+  // the K npad values are the diagonal, then (K-1)/2 blocks of npad value pairs
+  // (entries 1+2q and 2+2q of a row); cpair holds the matching column pairs as
+  // two int16 in one 32-bit word. Null when the plain ELL form is used.
+  const float *vpair;
+  const uint32_t *cpair;
   const void *lval;
   const void *luval;
   const int32_t *lev_ptr;

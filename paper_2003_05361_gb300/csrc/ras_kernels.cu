@@ -730,16 +730,20 @@ __device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
 //   w = A r, gamma' = (r, r), delta' = (w, r)   (one fused reduction),
 //   beta' = gamma'/gamma, alpha' = gamma' / (delta' - beta' gamma'/alpha).
 // A_p is staged in shared memory (FP32 values, int16 local columns, the
-// diagonal first in every row). r lives in shared memory (the operand of the
+// diagonal first in every row; PAIRED: the off-diagonal values and columns in
+// pairs, one 64-bit and one 32-bit load per two entries). r lives in shared memory (the operand of the
 // products, read once per step per row and reused); p, s, d, w live in
 // registers: thread t owns rows t, t + NT, ... On entry r holds the local
 // residual (zero beyond n); on exit it holds d. KC > 0 is the ELL width known
 // at compile time (KC = 0: runtime K). red holds 4 * NT/32 floats.
-template <int NT, int RMAX, int KC>
+template <int NT, int RMAX, int KC, bool PAIRED>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
                                 int m, float *r, float *red) {
+  static_assert(!PAIRED || (KC > 0 && KC % 2 == 1), "pairs need an odd compile-time width");
   const int tid = threadIdx.x;
   float *red0 = red, *red1 = red + 2 * (NT / 32);
+  const float2 *vp = reinterpret_cast<const float2 *>(sval + npad);
+  const uint32_t *cp = reinterpret_cast<const uint32_t *>(scol);
   float p[RMAX], s[RMAX], d[RMAX], w[RMAX];
   // w = A r and the two products of r
   auto product = [&](float &gam, float &del) {
@@ -752,7 +756,15 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
       if (i < n) {
         const float ri = r[i];
         wi = sval[i] * ri;
-        if constexpr (KC > 0) {
+        if constexpr (PAIRED) {
+#pragma unroll
+          for (int q = 0; q < (KC - 1) / 2; ++q) {
+            const float2 v = vp[q * npad + i];
+            const uint32_t c = cp[q * npad + i];
+            wi += v.x * r[c & 0xffffu];
+            wi += v.y * r[c >> 16];
+          }
+        } else if constexpr (KC > 0) {
 #pragma unroll
           for (int e = 1; e < KC; ++e) wi += sval[e * npad + i] * r[scol[e * npad + i]];
         } else {
@@ -1105,13 +1117,20 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kCGS && tid == 0) {
       // stage A_p (values, columns) while the residual is gathered
       const size_t vl = SM::vec_len(L.npad_max);
-      const uint32_t bv = (uint32_t)((size_t)K * D.npad * 4), bc = (uint32_t)((size_t)K * D.npad * 2);
+      const bool pr = S.vpair != nullptr;
+      const uint32_t bv = (uint32_t)((size_t)K * D.npad * 4);
+      const uint32_t bc = (uint32_t)((size_t)(pr ? K - 1 : K) * D.npad * 2);
       fence_proxy_async();
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_mbar[0])),
                    "r"(bv + bc)
                    : "memory");
-      bulk_copy_nobar_arrive(smem, reinterpret_cast<const float *>(S.lval) + D.row_off * K, bv, &s_mbar[0]);
-      bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.lcol16 + D.row_off * K, bc, &s_mbar[0]);
+      if (pr) {
+        bulk_copy_nobar_arrive(smem, S.vpair + D.row_off * K, bv, &s_mbar[0]);
+        bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.cpair + D.row_off * K / 2, bc, &s_mbar[0]);
+      } else {
+        bulk_copy_nobar_arrive(smem, reinterpret_cast<const float *>(S.lval) + D.row_off * K, bv, &s_mbar[0]);
+        bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.lcol16 + D.row_off * K, bc, &s_mbar[0]);
+      }
     }
     double a_loc = 0.0, a_own = 0.0;
     if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
@@ -1151,9 +1170,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       float *pv = reinterpret_cast<float *>(v0);
       float *rd = reinterpret_cast<float *>(s_redc);
       constexpr int RM = (kStagedRows + NT - 1) / NT;
-      if (K == 5) cg_solve_staged<NT, RM, 5>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
-      else if (K == 7) cg_solve_staged<NT, RM, 7>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
-      else cg_solve_staged<NT, RM, 0>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      if (S.vpair && K == 5) cg_solve_staged<NT, RM, 5, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else if (S.vpair && K == 7) cg_solve_staged<NT, RM, 7, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else if (S.vpair && K == 3) cg_solve_staged<NT, RM, 3, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else if (K == 5) cg_solve_staged<NT, RM, 5, false>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else if (K == 7) cg_solve_staged<NT, RM, 7, false>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      else cg_solve_staged<NT, RM, 0, false>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
       delta = v0;
     } else if (KIND == kCG) {
       const int32_t *lc = S.lcol + D.row_off * K;
