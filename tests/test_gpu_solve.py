@@ -120,6 +120,31 @@ def test_sync_converged_matches_oracle(kind):
     assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_staged_fp32_cg_iterates_match_oracle_fp32(dim):
+    # the shared-memory staged FP32 CG (Chronopoulos-Gear arrangement, entries
+    # in pairs: ELL width 5 in 2D, 7 in 3D) against the oracle's FP32 textbook
+    # CG: after 20 local steps the synchronous iterates agree to the FP32
+    # rounding the two summation orders leave; a wrong step length, sign or
+    # pairing moves them by orders of magnitude more
+    if dim == 2:
+        A = problems.poisson2d(45)
+        P, part = 6, ras.ras_partition_regular2d(45, 45, 3, 2)
+    else:
+        A = problems.poisson3d(14)
+        P, part = 4, ras.ras_partition_bfs(problems.poisson3d(14), 4, 7)
+    b = problems.rhs_uniform(A.n, 12)
+    ctx = ras.ras_setup(A, part, P, 2, CG, F32, 20)
+    assert ras.ras_get_launch(ctx)["kernel_variant"] == 3  # the staged kernel ran
+    for k in (1, 3):
+        x, info = gpu_solve(A, b, part, P, 2, CG, F32, 20, max_updates=k, ctx=ctx)
+        assert info.iterations == k
+        xo = oracle.ras_sync(A, b, part, P, 2, oracle.CG, oracle.FP32, 20, tol=0.0, max_iter=k,
+                             allow_noconv=True)[0]
+        assert np.linalg.norm(x - xo) <= 2e-4 * np.linalg.norm(xo), k
+    ras.ras_destroy(ctx)
+
+
 # ---------------------------------------------------------------- mixed precision
 
 @pytest.mark.parametrize("kind,prec", [(BAND, F32), (BAND, BF16), (CG, F32), (ILU, F32)])
