@@ -100,8 +100,9 @@ typedef struct {
   int32_t status;         /* same as the return value of the solve */
   double kernel_ms;       /* device time of the persistent RAS kernel alone */
   int64_t stale_updates;  /* async: local solves that saw no new neighbour data */
-  int32_t error_site;     /* RAS_ETIMEOUT only: 1 grid barrier, 2 band-slab copy, 3 async
-                             idle wait, 4 whole-solve time limit, 5 staged-matrix copy */
+  int32_t error_site;     /* RAS_ETIMEOUT only: 1 grid barrier, 3 async idle wait,
+                             4 whole-solve time limit, 5 staged-matrix copy (2 is not
+                             used: the band copies complete by construction) */
   int32_t reserved_;
 } ras_solve_info;
 

@@ -917,7 +917,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   CUDA_TRY(cudaMemsetAsync(c->d_xalt, 0, sizeof(double) * n, c->stream));
 
   if (kind == RAS_LOCAL_BANDCHOL) {
-    // factorise on the GPU in FP64, then lay out the slabs in the storage precision
+    // factorise on the GPU in FP64, then lay out the block records in the storage precision
     double *d_band = nullptr;
     BandJob *d_jobs = nullptr;
     LayoutJob *d_ljobs = nullptr;

@@ -10,7 +10,7 @@
 //     entry k of local row i at row_off*K + k*npad + i). It computes
 //     r_p = b[Omega_p] - A[Omega_p, :] x, reading x on Omega_p and E_p;
 //   * the owned-row list own_l (local ids);
-//   * local-solver data: banded-Cholesky slabs (fac), or the local matrix A_p
+//   * local-solver data: banded-Cholesky block records (fac), or the local matrix A_p
 //     in ELL form with LOCAL columns (lcol/lval) plus ILU(0) factors (luval)
 //     and level schedules.
 #pragma once
@@ -32,10 +32,10 @@ struct SubDesc {
   int32_t n;        // |Omega_p|
   int32_t npad;     // n rounded up to a multiple of 32
   int32_t n_own;    // |O_p|
-  int32_t W;        // band: half-bandwidth w (>= 1); slab = 32 * W entries
+  int32_t W;        // band: half-bandwidth w rounded up to a multiple of 4 (>= 4)
   int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
   int64_t own_off;  // offset into own_l
-  int64_t fac_off;  // band: forward slabs, backward slabs, packed inverse blocks
+  int64_t fac_off;  // band: nb forward records, then nb backward records (32 x (W+32) each)
   int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
   int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
   int32_t nlev_f;   // ILU: number of forward / backward levels
@@ -152,7 +152,7 @@ struct Launch {
   int32_t npad_max;
   int32_t persist;             // async: keep polling until every system is done
   int32_t kmax;                // largest ELL width over the launch
-  int32_t nstages;             // band: slab ring depth (2..8)
+  int32_t nstages;             // band: copy pipeline depth in chain steps (4 or 6)
   int32_t fresh;               // async: update only after a neighbour published since the last update
 };
 

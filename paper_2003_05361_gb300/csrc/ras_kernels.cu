@@ -4,9 +4,10 @@
 //   band_chol_kernel     setup: banded Cholesky A_p = L L^T in FP64, one CTA per
 //                        subdomain, sliding (w+1)x(w+1) window in shared memory
 //                        (direct local solver of Sec. 3.3.1, factorised once).
-//   band_layout_kernel   setup: turns L into the slab layout read by the
-//                        triangular solves (inverted 32x32 diagonal blocks),
-//                        rounded to the storage precision (FP64 / FP32 / BF16).
+//   band_layout_kernel   setup: turns L into the per-block records read by the
+//                        chained triangular solves ([inverse 32x32 diagonal
+//                        block | window operator]), rounded to the storage
+//                        precision (FP64 / FP32 / BF16).
 //   ras_init_kernel      per solve: ||b||^2 over Omega_p and O_p, state reset.
 //   ras_sysnorm_kernel   per solve: per-system sums in a fixed order.
 //   ras_main_kernel      the persistent RAS kernel, one CTA per group of
@@ -17,14 +18,17 @@
 //                        neighbours acquire it before reading (asynchronous
 //                        Schwarz, Sec. 2.1 / one-sided exchange of Sec. 3.4);
 //                        convergence by the local criterion of Eq. 2, a global
-//                        converged counter, and the post-termination global
-//                        check of Sec. 3.3.2.
+//                        converged counter (RAS_ASYNC) or flags flooded
+//                        between neighbours (RAS_ASYNC_DECENTRAL), and the
+//                        post-termination global check of Sec. 3.3.2.
 //   ras_residual_kernel  ||b - A x||^2 partials over owned rows.
 //   ras_copyback_kernel  moves a sync result left in the second buffer to x.
 //
-// Every device-side wait (grid barrier, mbarrier, idle polling) is bounded by
-// a %globaltimer limit; on expiry the kernel records RAS_ETIMEOUT in GridCtl,
-// raises the abort flag, drains its own bulk copies and returns.
+// Every device-side wait (grid barrier, the staged CG's mbarrier, idle
+// polling) is bounded by a %globaltimer limit; on expiry the kernel records
+// RAS_ETIMEOUT in GridCtl, raises the abort flag, drains its own bulk copies
+// and returns. The band chain's cp.async copies are waited for with
+// cp.async.wait_group, which completes by construction.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -211,7 +215,8 @@ __device__ bool grid_barrier(GridCtl *c, int fin, int64_t timeout_ns, int *s_fla
 }
 
 // --------------------------------------------------------------------------
-// bulk-copy (TMA) helpers for the band slabs
+// asynchronous copies: 1D bulk copies (TMA) with an mbarrier for the staged CG,
+// per-thread cp.async for the band chain
 // --------------------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -219,17 +224,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
-                                            uint64_t *bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
 }
 __device__ __forceinline__ void bulk_copy_nobar_arrive(void *dst, const void *src, uint32_t bytes,
                                                        uint64_t *bar) {

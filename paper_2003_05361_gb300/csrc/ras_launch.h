@@ -15,11 +15,11 @@ struct BandJob {
   int64_t band_off;  // offset of the row-major band (ld = w+1) in the FP64 scratch
 };
 
-// One 32-row block of one subdomain for the slab layout.
+// One 32-row block of one subdomain for the record layout.
 struct LayoutJob {
   int32_t n, w, W, K, nb, pad_;
   int64_t band_off;  // FP64 band of the subdomain
-  int64_t fac_off;   // first slab of the subdomain (entries)
+  int64_t fac_off;   // first record of the subdomain (entries)
 };
 
 size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax, int nstages);
