@@ -168,7 +168,10 @@ struct ras_ctx {
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
   uint8_t *d_ownf = nullptr;
   double *d_rval = nullptr, *d_xalt = nullptr, *d_xg = nullptr;
-  void *d_fac = nullptr, *d_lval = nullptr, *d_lu = nullptr;
+  void *d_fac = nullptr, *d_lval = nullptr;
+  int32_t *d_ifc = nullptr, *d_ibc = nullptr;  // ILU(0) factors in level order
+  void *d_ifv = nullptr, *d_ibv = nullptr, *d_ibd = nullptr;
+  int32_t ilu_kl = 0, ilu_ku = 0;
   int64_t device_bytes = 0;
   // launch state
   LaunchPlan plan;
@@ -536,7 +539,13 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.vpair = c->d_vpair;
   s.cpair = c->d_cpair;
   s.lval = c->d_lval;
-  s.luval = c->d_lu;
+  s.ilu_fcol = c->d_ifc;
+  s.ilu_fval = c->d_ifv;
+  s.ilu_bcol = c->d_ibc;
+  s.ilu_bval = c->d_ibv;
+  s.ilu_bdiag = c->d_ibd;
+  s.ilu_kl = c->ilu_kl;
+  s.ilu_ku = c->ilu_ku;
   s.lev_ptr = c->d_levp;
   s.lev_rows = c->d_levr;
   s.nbr = c->d_nbr;
@@ -1012,7 +1021,66 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     };
     if ((st = up_prec(c->d_lval, lval64)) != RAS_OK) return st;
     if (kind == RAS_LOCAL_ILU0_CG) {
-      if ((st = up_prec(c->d_lu, lu64)) != RAS_OK) return st;
+      {
+        // level-order copies of the factors: forward rows keep their strictly
+        // lower entries, backward rows their strictly upper ones and the
+        // diagonal, each in the ELL order of the row
+        int kl = 0, ku = 0;
+        for (int p = 0; p < P; ++p) {
+          const SubDesc &d = c->subs[p];
+          for (int i = 0; i < d.n; ++i) {
+            int nl = 0, nu = 0;
+            for (int k = 0; k < K; ++k) {
+              const int64_t e = d.row_off * K + (int64_t)k * d.npad + i;
+              if (lu64[e] == 0.0) continue;
+              if (lc[e] < i) ++nl;
+              else if (lc[e] > i) ++nu;
+            }
+            kl = std::max(kl, nl);
+            ku = std::max(ku, nu);
+          }
+        }
+        kl = std::max(kl, 1);
+        ku = std::max(ku, 1);
+        c->ilu_kl = kl;
+        c->ilu_ku = ku;
+        std::vector<int32_t> fc(rows * kl, -1), bc(rows * ku, -1);
+        std::vector<double> fv(rows * kl, 0.0), bv(rows * ku, 0.0), bd(rows, 1.0);
+        for (int p = 0; p < P; ++p) {
+          const SubDesc &d = c->subs[p];
+          const int32_t *rf = levr_all.data() + d.lrow_off, *rb = rf + d.n;
+          for (int e = 0; e < d.n; ++e) {
+            int t = 0;
+            const int i = rf[e];
+            for (int k = 0; k < K; ++k) {
+              const int64_t q = d.row_off * K + (int64_t)k * d.npad + i;
+              if (lu64[q] != 0.0 && lc[q] < i) {
+                fc[d.row_off * kl + (int64_t)t * d.npad + e] = lc[q];
+                fv[d.row_off * kl + (int64_t)t * d.npad + e] = lu64[q];
+                ++t;
+              }
+            }
+            t = 0;
+            const int ib = rb[e];
+            for (int k = 0; k < K; ++k) {
+              const int64_t q = d.row_off * K + (int64_t)k * d.npad + ib;
+              if (lu64[q] == 0.0) continue;
+              if (lc[q] > ib) {
+                bc[d.row_off * ku + (int64_t)t * d.npad + e] = lc[q];
+                bv[d.row_off * ku + (int64_t)t * d.npad + e] = lu64[q];
+                ++t;
+              } else if (lc[q] == ib) {
+                bd[d.row_off + e] = lu64[q];
+              }
+            }
+          }
+        }
+        if ((st = c->upload(c->d_ifc, fc)) != RAS_OK) return st;
+        if ((st = c->upload(c->d_ibc, bc)) != RAS_OK) return st;
+        if ((st = up_prec(c->d_ifv, fv)) != RAS_OK) return st;
+        if ((st = up_prec(c->d_ibv, bv)) != RAS_OK) return st;
+        if ((st = up_prec(c->d_ibd, bd)) != RAS_OK) return st;
+      }
       if ((st = c->upload(c->d_levp, levp_all)) != RAS_OK) return st;
       if ((st = c->upload(c->d_levr, levr_all)) != RAS_OK) return st;
     }

@@ -106,7 +106,18 @@ struct SysDesc {
   const float *vpair;
   const uint32_t *cpair;
   const void *lval;
-  const void *luval;
+  // ILU(0) factors in level order: forward sweep row e (lev_rows, forward
+  // part) has its strictly lower entries at ilu_fcol / ilu_fval[k*npad + e]
+  // (k < ilu_kl, column -1 = none), backward sweep row e its strictly upper
+  // entries at ilu_bcol / ilu_bval[k*npad + e] (k < ilu_ku) and its diagonal
+  // at ilu_bdiag[e]; per subdomain from row_off * ilu_kl, row_off * ilu_ku,
+  // row_off. Values in the storage precision.
+  const int32_t *ilu_fcol;
+  const void *ilu_fval;
+  const int32_t *ilu_bcol;
+  const void *ilu_bval;
+  const void *ilu_bdiag;
+  int32_t ilu_kl, ilu_ku;
   const int32_t *lev_ptr;
   const int32_t *lev_rows;
   const int32_t *nbr;
@@ -121,6 +132,7 @@ struct Item {
 
 constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
 constexpr int kMaxEll = 8;      // ELL widths up to this are fully unrolled
+constexpr int kIluHalf = 4;     // ILU(0): strictly lower / upper entries per row kept in registers
 constexpr int kStagedRows = 6144;  // largest subdomain of the staged CG variant
 
 struct GridCtl {

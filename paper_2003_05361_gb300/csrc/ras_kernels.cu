@@ -815,39 +815,106 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
 }
 
 // z = U^{-1} L^{-1} r with the ILU(0) factors, level by level.
+// One triangular sweep of the ILU(0) solve: level rows e in
+// [lptr[lv], lptr[lv+1]); the entries of level row e sit at index e
+// (cc / vv[k*npad + e], column -1 = none), so a row's loads do not wait for
+// its row number. BACK: U sweep (z[i] = (z[i] - sum) / d[e]), else L sweep
+// (z[i] = r[i] - sum). With KE <= kIluHalf each thread's first row of level
+// lv+1 is loaded into registers while level lv is computed, so the barrier
+// between levels hides the load latency.
+template <typename T, typename CT, int NT, bool BACK>
+__device__ __forceinline__ void ilu_sweep(const int32_t *__restrict__ lptr, int nl,
+                                          const int32_t *__restrict__ lrow,
+                                          const int32_t *__restrict__ cc, const T *__restrict__ vv,
+                                          const T *__restrict__ dd, int KE, int npad, const CT *r,
+                                          CT *z) {
+  constexpr int H = kIluHalf;
+  if (nl <= 0) return;
+  const int tid = threadIdx.x;
+  const bool reg = KE <= H;
+  int a = __ldg(lptr), b = __ldg(lptr + 1);
+  int ri = -1, ci[H];
+  CT cv[H], dg = CT(1);
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    ci[q] = -1;
+    cv[q] = CT(0);
+  }
+  if (reg && a + tid < b) {
+    const int e = a + tid;
+    ri = __ldg(lrow + e);
+#pragma unroll
+    for (int q = 0; q < H; ++q)
+      if (q < KE) {
+        ci[q] = __ldg(cc + (int64_t)q * npad + e);
+        cv[q] = to_ct(vv[(int64_t)q * npad + e]);
+      }
+    if (BACK) dg = to_ct(dd[e]);
+  }
+  for (int lv = 0; lv < nl; ++lv) {
+    const int b2 = lv + 1 < nl ? __ldg(lptr + lv + 2) : b;
+    // next level's first row of this thread
+    int ni = -1, nc[H];
+    CT nv[H], nd = CT(1);
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      nc[q] = -1;
+      nv[q] = CT(0);
+    }
+    if (reg && b + tid < b2) {
+      const int e = b + tid;
+      ni = __ldg(lrow + e);
+#pragma unroll
+      for (int q = 0; q < H; ++q)
+        if (q < KE) {
+          nc[q] = __ldg(cc + (int64_t)q * npad + e);
+          nv[q] = to_ct(vv[(int64_t)q * npad + e]);
+        }
+      if (BACK) nd = to_ct(dd[e]);
+    }
+    if (ri >= 0) {
+      CT s = BACK ? z[ri] : r[ri];
+#pragma unroll
+      for (int q = 0; q < H; ++q)
+        if (ci[q] >= 0) s -= cv[q] * z[ci[q]];
+      z[ri] = BACK ? s / dg : s;
+    }
+    // rows beyond the first per thread (wide levels), or all rows when KE > H
+    for (int e = a + tid + (reg ? NT : 0); e < b; e += NT) {
+      const int i = __ldg(lrow + e);
+      CT s = BACK ? z[i] : r[i];
+      for (int q = 0; q < KE; ++q) {
+        const int c = __ldg(cc + (int64_t)q * npad + e);
+        if (c >= 0) s -= to_ct(vv[(int64_t)q * npad + e]) * z[c];
+      }
+      z[i] = BACK ? s / to_ct(dd[e]) : s;
+    }
+    __syncthreads();
+    ri = ni;
+    dg = nd;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      ci[q] = nc[q];
+      cv[q] = nv[q];
+    }
+    a = b;
+    b = b2;
+  }
+}
+
+// z = U^{-1} L^{-1} r with the ILU(0) factors in level order.
 template <typename T, typename CT, int NT>
-__device__ __forceinline__ void ilu_apply(const int32_t *lc, const T *lu, int K, int npad,
-                                          const int32_t *lptr_f, int nlf, const int32_t *lrow_f,
-                                          const int32_t *lptr_b, int nlb, const int32_t *lrow_b,
-                                          const CT *r, CT *z) {
-  for (int lv = 0; lv < nlf; ++lv) {
-    const int a = lptr_f[lv], b = lptr_f[lv + 1];
-    for (int e = a + threadIdx.x; e < b; e += NT) {
-      const int i = lrow_f[e];
-      CT s = r[i];
-      for (int k = 0; k < K; ++k) {
-        const int c = lc[(int64_t)k * npad + i];
-        if (c < i) s -= to_ct(lu[(int64_t)k * npad + i]) * z[c];
-      }
-      z[i] = s;
-    }
-    __syncthreads();
-  }
-  for (int lv = 0; lv < nlb; ++lv) {
-    const int a = lptr_b[lv], b = lptr_b[lv + 1];
-    for (int e = a + threadIdx.x; e < b; e += NT) {
-      const int i = lrow_b[e];
-      CT s = z[i], dg = CT(1);
-      for (int k = 0; k < K; ++k) {
-        const int c = lc[(int64_t)k * npad + i];
-        const CT v = to_ct(lu[(int64_t)k * npad + i]);
-        if (c > i) s -= v * z[c];
-        else if (c == i && v != CT(0)) dg = v;  // zero-valued padding entries also use c == i
-      }
-      z[i] = s / dg;
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void ilu_apply(const SysDesc &S, const SubDesc &D, const int32_t *lptr_f,
+                                          const int32_t *lrow_f, const int32_t *lptr_b,
+                                          const int32_t *lrow_b, const CT *r, CT *z) {
+  const int npad = D.npad, KL = S.ilu_kl, KU = S.ilu_ku;
+  const int32_t *fc = S.ilu_fcol + D.row_off * KL;
+  const T *fv = reinterpret_cast<const T *>(S.ilu_fval) + D.row_off * KL;
+  const int32_t *bc = S.ilu_bcol + D.row_off * KU;
+  const T *bv = reinterpret_cast<const T *>(S.ilu_bval) + D.row_off * KU;
+  const T *bd = reinterpret_cast<const T *>(S.ilu_bdiag) + D.row_off;
+  ilu_sweep<T, CT, NT, false>(lptr_f, D.nlev_f, lrow_f, fc, fv, bd, KL, npad, r, z);
+  ilu_sweep<T, CT, NT, true>(lptr_b, D.nlev_b, lrow_b, bc, bv, bd, KU, npad, r, z);
 }
 
 // m steps of ILU(0)-preconditioned CG from d = 0 (all threads).
@@ -857,7 +924,6 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
   const int K = S.K, n = D.n, npad = D.npad;
   const int32_t *lc = S.lcol + D.row_off * K;
   const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
-  const T *lu = reinterpret_cast<const T *>(S.luval) + D.row_off * K;
   const int32_t *lptr_f = S.lev_ptr + D.lev_off;
   const int32_t *lptr_b = lptr_f + D.nlev_f + 1;
   const int32_t *lrow_f = S.lev_rows + D.lrow_off;
@@ -868,7 +934,7 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
     d[i] = CT(0);
   }
   __syncthreads();
-  ilu_apply<T, CT, NT>(lc, lu, K, npad, lptr_f, D.nlev_f, lrow_f, lptr_b, D.nlev_b, lrow_b, r, z);
+  ilu_apply<T, CT, NT>(S, D, lptr_f, lrow_f, lptr_b, lrow_b, r, z);
   CT rz = CT(0);
   for (int i = threadIdx.x; i < npad; i += NT) {
     p[i] = z[i];
@@ -890,7 +956,7 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
       r[i] -= alpha * q[i];
     }
     __syncthreads();
-    ilu_apply<T, CT, NT>(lc, lu, K, npad, lptr_f, D.nlev_f, lrow_f, lptr_b, D.nlev_b, lrow_b, r, z);
+    ilu_apply<T, CT, NT>(S, D, lptr_f, lrow_f, lptr_b, lrow_b, r, z);
     CT rn = CT(0);
     for (int i = threadIdx.x; i < n; i += NT) rn += r[i] * z[i];
     rn = block_sum<NT, CT>(rn, red);
