@@ -819,9 +819,37 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
 // [lptr[lv], lptr[lv+1]); the entries of level row e sit at index e
 // (cc / vv[k*npad + e], column -1 = none), so a row's loads do not wait for
 // its row number. BACK: U sweep (z[i] = (z[i] - sum) / d[e]), else L sweep
-// (z[i] = r[i] - sum). With KE <= kIluHalf each thread's first row of level
-// lv+1 is loaded into registers while level lv is computed, so the barrier
-// between levels hides the load latency.
+// (z[i] = r[i] - sum). With KE <= kIluHalf each thread's first rows of levels
+// lv+1 and lv+2 are loaded into registers while level lv is computed, so the
+// barriers between levels hide the load latency.
+template <typename T, int NT, bool BACK>
+struct IluRow {
+  int i, c[kIluHalf];
+  typename CTypeOf<T>::type v[kIluHalf], d;
+  __device__ __forceinline__ void load(int e, int end, bool reg, const int32_t *__restrict__ lrow,
+                                       const int32_t *__restrict__ cc, const T *__restrict__ vv,
+                                       const T *__restrict__ dd, int KE, int npad) {
+    using CT = typename CTypeOf<T>::type;
+    i = -1;
+    d = CT(1);
+#pragma unroll
+    for (int q = 0; q < kIluHalf; ++q) {
+      c[q] = -1;
+      v[q] = CT(0);
+    }
+    if (reg && e < end) {
+      i = __ldg(lrow + e);
+#pragma unroll
+      for (int q = 0; q < kIluHalf; ++q)
+        if (q < KE) {
+          c[q] = __ldg(cc + (int64_t)q * npad + e);
+          v[q] = to_ct(vv[(int64_t)q * npad + e]);
+        }
+      if (BACK) d = to_ct(dd[e]);
+    }
+  }
+};
+
 template <typename T, typename CT, int NT, bool BACK>
 __device__ __forceinline__ void ilu_sweep(const int32_t *__restrict__ lptr, int nl,
                                           const int32_t *__restrict__ lrow,
@@ -832,52 +860,21 @@ __device__ __forceinline__ void ilu_sweep(const int32_t *__restrict__ lptr, int 
   if (nl <= 0) return;
   const int tid = threadIdx.x;
   const bool reg = KE <= H;
+  // level bounds of lv, lv+1, lv+2: [a, b), [b, b2), [b2, b3)
   int a = __ldg(lptr), b = __ldg(lptr + 1);
-  int ri = -1, ci[H];
-  CT cv[H], dg = CT(1);
-#pragma unroll
-  for (int q = 0; q < H; ++q) {
-    ci[q] = -1;
-    cv[q] = CT(0);
-  }
-  if (reg && a + tid < b) {
-    const int e = a + tid;
-    ri = __ldg(lrow + e);
-#pragma unroll
-    for (int q = 0; q < H; ++q)
-      if (q < KE) {
-        ci[q] = __ldg(cc + (int64_t)q * npad + e);
-        cv[q] = to_ct(vv[(int64_t)q * npad + e]);
-      }
-    if (BACK) dg = to_ct(dd[e]);
-  }
+  int b2 = nl > 1 ? __ldg(lptr + 2) : b;
+  IluRow<T, NT, BACK> cur, nx1, nx2;
+  cur.load(a + tid, b, reg, lrow, cc, vv, dd, KE, npad);
+  nx1.load(b + tid, b2, reg, lrow, cc, vv, dd, KE, npad);
   for (int lv = 0; lv < nl; ++lv) {
-    const int b2 = lv + 1 < nl ? __ldg(lptr + lv + 2) : b;
-    // next level's first row of this thread
-    int ni = -1, nc[H];
-    CT nv[H], nd = CT(1);
-#pragma unroll
-    for (int q = 0; q < H; ++q) {
-      nc[q] = -1;
-      nv[q] = CT(0);
-    }
-    if (reg && b + tid < b2) {
-      const int e = b + tid;
-      ni = __ldg(lrow + e);
+    const int b3 = lv + 2 < nl ? __ldg(lptr + lv + 3) : b2;
+    nx2.load(b2 + tid, b3, reg, lrow, cc, vv, dd, KE, npad);
+    if (cur.i >= 0) {
+      CT s = BACK ? z[cur.i] : r[cur.i];
 #pragma unroll
       for (int q = 0; q < H; ++q)
-        if (q < KE) {
-          nc[q] = __ldg(cc + (int64_t)q * npad + e);
-          nv[q] = to_ct(vv[(int64_t)q * npad + e]);
-        }
-      if (BACK) nd = to_ct(dd[e]);
-    }
-    if (ri >= 0) {
-      CT s = BACK ? z[ri] : r[ri];
-#pragma unroll
-      for (int q = 0; q < H; ++q)
-        if (ci[q] >= 0) s -= cv[q] * z[ci[q]];
-      z[ri] = BACK ? s / dg : s;
+        if (cur.c[q] >= 0) s -= cur.v[q] * z[cur.c[q]];
+      z[cur.i] = BACK ? s / cur.d : s;
     }
     // rows beyond the first per thread (wide levels), or all rows when KE > H
     for (int e = a + tid + (reg ? NT : 0); e < b; e += NT) {
@@ -890,15 +887,11 @@ __device__ __forceinline__ void ilu_sweep(const int32_t *__restrict__ lptr, int 
       z[i] = BACK ? s / to_ct(dd[e]) : s;
     }
     __syncthreads();
-    ri = ni;
-    dg = nd;
-#pragma unroll
-    for (int q = 0; q < H; ++q) {
-      ci[q] = nc[q];
-      cv[q] = nv[q];
-    }
+    cur = nx1;
+    nx1 = nx2;
     a = b;
     b = b2;
+    b2 = b3;
   }
 }
 
