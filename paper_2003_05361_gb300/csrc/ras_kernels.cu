@@ -1431,13 +1431,20 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
         any_work = 1;
         const int epoch = (int)(wd >> 2);
         if (action == 1) {
-          // acquire the neighbours' published versions before reading x
-          if (tid == 0) {
+          // acquire the neighbours' published versions before reading x: the
+          // lanes of warp 0 take one neighbour each, so the acquires are in
+          // flight together; the barrier then orders every thread's reads of
+          // x after them
+          if (tid < 32) {
             uint64_t seen = 0;
             const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-            for (int q = 0; q < s_sub.n_nbr; ++q) seen += ld_acquire_u32(&s_sys.sub[nb[q]].version);
-            if (ss.updates > 0 && seen == ss.nbr_seen) ss.stale += 1;
-            ss.nbr_seen = seen;
+            for (int q = tid; q < s_sub.n_nbr; q += 32) seen += ld_acquire_u32(&s_sys.sub[nb[q]].version);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(0xffffffffu, seen, o);
+            if (tid == 0) {
+              if (ss.updates > 0 && seen == ss.nbr_seen) ss.stale += 1;
+              ss.nbr_seen = seen;
+            }
           }
           __syncthreads();
           double rl, ro;
