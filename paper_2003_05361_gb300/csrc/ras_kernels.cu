@@ -1143,6 +1143,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
+  if (tid == 0) s_flag[7] = -1;  // no system descriptor loaded yet
   for (int k = tid; k < nls; k += NT) {
     const int sys = L.cta_sys[2 * (cs0 + k)];
     s_done[k] = L.sys[sys].st->done;  // systems finished in an earlier launch stay finished
@@ -1287,7 +1288,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     __syncthreads();  // everyone is done with the previous item's shared state
     if (tid == 0) {
       const Item item = L.items[it];
-      s_sys = L.sys[item.sys];
+      if (item.sys != s_flag[7]) {  // the system descriptor is constant in a launch
+        s_sys = L.sys[item.sys];
+        s_flag[7] = item.sys;
+      }
       s_sub = s_sys.subs[item.p];
       s_flag[5] = item.p;
       s_flag[6] = item.ls;
@@ -1450,7 +1454,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
           double rl, ro;
           if (!update(s_sys.x, s_sys.x, rl, ro)) goto out;
           if (tid == 0) {
-            __threadfence();
+            // every thread fenced its owned-row stores before update()'s
+            // final barrier; the release store publishes them
             ss.updates += 1;
             ss.step_updates += 1;
             st_release_u32(&ss.version, (uint32_t)ss.updates);
