@@ -1126,6 +1126,7 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   // failed global check is routine there: it resumes until max_updates
   L.max_restarts = mode == RAS_ASYNC_DECENTRAL ? (1 << 30) : 8;
   L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
+  L.consistent = (int32_t)env_int("RAS_ASYNC_CONSISTENT", 0);
   L.m = m;
   L.Wmax = pl.Wmax;
   L.npad_max = pl.npad_max;
@@ -1433,6 +1434,7 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   // failed global check is routine there: it resumes until max_updates
   L.max_restarts = mode == RAS_ASYNC_DECENTRAL ? (1 << 30) : 8;
   L.fresh = (int32_t)env_int("RAS_ASYNC_FRESH", 0);
+  L.consistent = (int32_t)env_int("RAS_ASYNC_CONSISTENT", 0);
   L.m = c0->ls.inner_iters;
   L.Wmax = sc.plan.Wmax;
   L.npad_max = sc.plan.npad_max;

@@ -55,7 +55,8 @@ struct SubState {
   uint64_t t_solve;   // accumulated ns in the local solve
   uint64_t t_update;  // accumulated ns in the restricted update + publish
   uint64_t nbr_seen;  // async: sum of neighbour versions at the last solve
-  uint32_t version;   // async: published update counter (release store)
+  uint32_t version;   // async: 2 x published updates (release store); odd while the
+                      // owned rows are being written (a sequence lock for readers)
   int32_t conv_epoch; // async: epoch in which Eq. 2 last held (-1: not converged)
   int32_t park_epoch;
   int32_t check_epoch;
@@ -166,6 +167,8 @@ struct Launch {
   int32_t kmax;                // largest ELL width over the launch
   int32_t nstages;             // band: copy pipeline depth in chain steps (4 or 6)
   int32_t fresh;               // async: update only after a neighbour published since the last update
+  int32_t consistent;          // async: redo a gather that overlapped a neighbour's write (<= 2 times)
+  int32_t pad3_;
 };
 
 }  // namespace ras

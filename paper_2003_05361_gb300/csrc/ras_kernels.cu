@@ -57,6 +57,9 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -1104,6 +1107,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   __shared__ double s_red[NT / 32 * 2];
   __shared__ __align__(16) CT s_redc[4 * (NT / 32)];
   __shared__ int s_flag[8];
+  __shared__ uint32_t s_seq[32];  // async: neighbours' sequence values seen before the gather
   __shared__ __align__(8) uint64_t s_mbar[1];
   __shared__ int s_done[kMaxCtaSys];
   __shared__ int64_t s_iter0[kMaxCtaSys];
@@ -1187,10 +1191,32 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       }
     }
     double a_loc = 0.0, a_own = 0.0;
-    if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
-    else if (K == 7) gather_rows<7, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
-    else gather_rows<0, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
-    block_sum2<NT>(a_loc, a_own, s_red);
+    for (int attempt = 0;; ++attempt) {
+      a_loc = 0.0;
+      a_own = 0.0;
+      if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+      else if (K == 7) gather_rows<7, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+      else gather_rows<0, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+      block_sum2<NT>(a_loc, a_own, s_red);
+      // asynchronous mode: a gather that overlapped a neighbour's write of its
+      // owned rows (its sequence value was odd, or moved) saw a mix of that
+      // neighbour's old and new values; it is redone, at most twice
+      if (!async || !L.consistent || attempt == 2 || D.n_nbr == 0 || D.n_nbr > 32) break;
+      __threadfence();  // this thread's reads of x before the re-read below
+      __syncthreads();
+      if (tid < 32) {
+        bool torn = false;
+        if (tid < D.n_nbr) {
+          const uint32_t now = ld_acquire_u32(&S.sub[S.nbr[D.nbr_off + tid]].version);
+          torn = (s_seq[tid] & 1u) || now != s_seq[tid];
+          s_seq[tid] = now;
+        }
+        torn = __any_sync(0xffffffffu, torn);
+        if (tid == 0) s_flag[3] = torn ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_flag[3]) break;
+    }
     res_loc = a_loc;
     res_own = a_own;
     if (tid == 0) t1 = gtimer();
@@ -1243,6 +1269,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       delta = v4;
     }
     if (tid == 0) t2 = gtimer();
+    if (async && L.consistent) {
+      // sequence value odd while the owned rows change
+      if (tid == 0) {
+        SubState &me = S.sub[s_flag[5]];
+        st_relaxed_u32(&me.version, (uint32_t)(2 * me.updates + 1));
+        __threadfence();
+      }
+      __syncthreads();
+    }
     // restricted prolongation: only owned rows are written (RAS). x_g + delta
     // on an owned row is the owned part of the local solution computed from
     // the very values this gather read, whatever other subdomains (or delays)
@@ -1442,7 +1477,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
           if (tid < 32) {
             uint64_t seen = 0;
             const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-            for (int q = tid; q < s_sub.n_nbr; q += 32) seen += ld_acquire_u32(&s_sys.sub[nb[q]].version);
+            for (int q = tid; q < s_sub.n_nbr; q += 32) {
+              const uint32_t v = ld_acquire_u32(&s_sys.sub[nb[q]].version);
+              seen += v;
+              if (q < 32) s_seq[q] = v;
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(0xffffffffu, seen, o);
             if (tid == 0) {
@@ -1458,7 +1497,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
             // final barrier; the release store publishes them
             ss.updates += 1;
             ss.step_updates += 1;
-            st_release_u32(&ss.version, (uint32_t)ss.updates);
+            st_release_u32(&ss.version, (uint32_t)(2 * ss.updates));
             // local criterion (Eq. 2) on the residual gathered before the update
             const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
             if (decentral) {

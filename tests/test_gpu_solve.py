@@ -231,6 +231,23 @@ def test_async_decentralized_irregular_partition_and_single_subdomain():
         assert true_relres(A, b, x) < 1e-8
 
 
+@pytest.mark.parametrize("kind,prec", [(BAND, F32), (CG, F32)])
+def test_async_consistent_gathers_converge(kind, prec, monkeypatch):
+    # the optional sequence-lock mode: a gather that overlapped a neighbour's
+    # write of its owned rows is redone; the result must meet the tolerance
+    # like any asynchronous run
+    monkeypatch.setenv("RAS_ASYNC_CONSISTENT", "1")
+    N = 64
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 3)
+    part = ras.ras_partition_regular2d(N, N, 4, 4)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    x, info = gpu_solve(A, b, part, 16, 2, kind, prec, 10, mode=ras.RAS_ASYNC, tol=1e-9)
+    assert info.status == 0, info.as_dict()
+    assert true_relres(A, b, x) < 1e-9
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
+
+
 @pytest.mark.parametrize("kind,prec", [(CG, F32), (ILU, F32), (BAND, F32)])
 def test_autotune_then_solve(kind, prec):
     N = 192
