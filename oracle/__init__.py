@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOTSPD, ENOCONV = 0, 1, 3, 4
-BANDCHOL, CG, ILU0_CG = 0, 1, 2
+BANDCHOL, CG, ILU0_CG, BANDLU, GMRES = 0, 1, 2, 3, 4
 FP64, FP32, BF16 = 0, 1, 2
 
 _I32P = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -67,6 +67,13 @@ def _load():
     lib.or_band_solve.restype = None
     lib.or_band_solve_lowp.argtypes = [C.c_int, C.c_int, _F64P, C.c_int, _F64P]
     lib.or_band_solve_lowp.restype = None
+    lib.or_band_lu.argtypes = [C.c_int, C.c_int, _F64P]
+    lib.or_band_lu_solve.argtypes = [C.c_int, C.c_int, _F64P, _F64P]
+    lib.or_band_lu_solve.restype = None
+    lib.or_band_lu_solve_lowp.argtypes = [C.c_int, C.c_int, _F64P, C.c_int, _F64P]
+    lib.or_band_lu_solve_lowp.restype = None
+    lib.or_gmres.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, C.c_int, C.c_int, _F64P]
+    lib.or_gmres.restype = None
     lib.or_dense_lu_solve.argtypes = [C.c_int, _F64P, _F64P]
     lib.or_cg.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, C.c_int, C.c_int, _F64P]
     lib.or_cg.restype = None
@@ -150,6 +157,33 @@ def band_solve(L: np.ndarray, w: int, rhs: np.ndarray, prec: int = FP64) -> np.n
     else:
         _load().or_band_solve_lowp(L.shape[0], w, Lc, prec, x)
     return x
+
+
+def band_lu(band: np.ndarray, w: int) -> np.ndarray:
+    """band: (n, 2w+1) array with band[i, t] = A[i, i-w+t]. Returns the LU factors
+    in the same layout (unit lower L below the diagonal, U on and above it)."""
+    F = np.ascontiguousarray(band, dtype=np.float64).copy()
+    rc = _load().or_band_lu(F.shape[0], w, F.reshape(-1))
+    if rc:
+        raise OracleError(f"band_lu: {rc}")
+    return F
+
+
+def band_lu_solve(F: np.ndarray, w: int, rhs: np.ndarray, prec: int = FP64) -> np.ndarray:
+    x = np.ascontiguousarray(rhs, dtype=np.float64).copy()
+    Fc = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    if prec == FP64:
+        _load().or_band_lu_solve(F.shape[0], w, Fc, x)
+    else:
+        _load().or_band_lu_solve_lowp(F.shape[0], w, Fc, prec, x)
+    return x
+
+
+def gmres(A, rhs: np.ndarray, m: int, prec: int = FP64) -> np.ndarray:
+    rp, ci, val = _csr(A)
+    d = np.empty(A.n)
+    _load().or_gmres(A.n, rp, ci, val, np.ascontiguousarray(rhs, dtype=np.float64), m, prec, d)
+    return d
 
 
 def dense_lu_solve(A: np.ndarray, b: np.ndarray) -> np.ndarray:

@@ -19,6 +19,8 @@
  *   Sec. 3.3.1          direct local solves: Cholesky factorisation once,
  *                       triangular solves every iteration; or an iterative
  *                       local solver (CG).
+ *   Sec. 4.1            a generic (nonsymmetric) system with LU or GMRES
+ *                       local solves.
  *   Sec. 3.3.2, Eq. 2   local criterion ||r_p||^2 < tau^2 ||b_p||^2 and the
  *                       global criterion ||r|| < tau ||b||.
  */
@@ -303,6 +305,73 @@ void or_band_solve_lowp(int n, int w, const double *L, int prec, double *x) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* local direct solver for general matrices: banded LU (Sec. 4.1 names LU   */
+/* as the local solver for a generic system)                                 */
+/* ------------------------------------------------------------------------ */
+
+#define BANDG(U, w, i, j) ((U)[(int64_t)(i) * (2 * (w) + 1) + ((j) - (i) + (w))])
+
+/* Doolittle LU without pivoting inside the band, row by row:
+ *   l_ij = (a_ij - sum_{k<j} l_ik u_kj) / u_jj   for j < i (unit lower L),
+ *   u_ij =  a_ij - sum_{k<i} l_ik u_kj           for j >= i,
+ * where only |i-k|, |k-j| <= w contribute. A zero pivot u_ii stops it. */
+int or_band_lu(int n, int w, double *band) {
+  for (int i = 0; i < n; ++i) {
+    int j0 = i - w > 0 ? i - w : 0;
+    int j1 = i + w < n - 1 ? i + w : n - 1;
+    for (int j = j0; j <= j1; ++j) {
+      double s = BANDG(band, w, i, j);
+      int k0 = j - w > j0 ? j - w : j0;
+      int k1 = (i < j ? i : j) - 1;
+      for (int k = k0; k <= k1; ++k) s -= BANDG(band, w, i, k) * BANDG(band, w, k, j);
+      if (j < i) {
+        BANDG(band, w, i, j) = s / BANDG(band, w, j, j);
+      } else {
+        if (j == i && !(fabs(s) > 0.0)) return OR_ENOTSPD;
+        BANDG(band, w, i, j) = s;
+      }
+    }
+  }
+  return OR_OK;
+}
+
+/* Forward substitution with the unit lower L, then backward with U. */
+void or_band_lu_solve(int n, int w, const double *LU, double *x) {
+  for (int i = 0; i < n; ++i) {
+    double s = x[i];
+    int k0 = i - w > 0 ? i - w : 0;
+    for (int k = k0; k < i; ++k) s -= BANDG(LU, w, i, k) * x[k];
+    x[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    int k1 = i + w < n - 1 ? i + w : n - 1;
+    for (int k = i + 1; k <= k1; ++k) s -= BANDG(LU, w, i, k) * x[k];
+    x[i] = s / BANDG(LU, w, i, i);
+  }
+}
+
+/* Same with the factors rounded to `prec` and FP32 arithmetic. */
+void or_band_lu_solve_lowp(int n, int w, const double *LU, int prec, double *x) {
+  float *y = (float *)malloc(sizeof(float) * (n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) y[i] = (float)x[i];
+  for (int i = 0; i < n; ++i) {
+    float s = y[i];
+    int k0 = i - w > 0 ? i - w : 0;
+    for (int k = k0; k < i; ++k) s -= or_round_storage(BANDG(LU, w, i, k), prec) * y[k];
+    y[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    float s = y[i];
+    int k1 = i + w < n - 1 ? i + w : n - 1;
+    for (int k = i + 1; k <= k1; ++k) s -= or_round_storage(BANDG(LU, w, i, k), prec) * y[k];
+    y[i] = s / or_round_storage(BANDG(LU, w, i, i), prec);
+  }
+  for (int i = 0; i < n; ++i) x[i] = (double)y[i];
+  free(y);
+}
+
+/* ------------------------------------------------------------------------ */
 /* dense LU with partial pivoting (for small-grid checks)                    */
 /* ------------------------------------------------------------------------ */
 
@@ -402,6 +471,96 @@ void or_cg(int n, const int32_t *rp, const int32_t *ci, const double *val, const
     for (int i = 0; i < n; ++i) d[i] = (double)x[i];
     free(r); free(p); free(q); free(x);
   }
+}
+
+/* Working-precision rounding for the GMRES below: in FP32 mode every
+ * operation's result is rounded to float. The operands are floats, so the
+ * double result of + - * / and sqrt rounded once more to float is the
+ * correctly rounded float result (double carries more than 2*24+2 bits;
+ * S. A. Figueroa, "When is double rounding innocuous?", SIGNUM 1995). */
+static double or_fl(int prec, double v) { return prec == OR_FP64 ? v : (double)(float)v; }
+
+/* m steps of GMRES (Saad & Schultz 1986) on A d = rhs from d = 0, one cycle:
+ * Arnoldi with modified Gram-Schmidt builds V (orthonormal) and the upper
+ * Hessenberg H with A V_k = V_{k+1} H; Givens rotations reduce H to upper
+ * triangular R and carry ||rhs|| e_1 along as g; then R y = g and
+ * d = V_k y, the vector of the Krylov space K_k(A, rhs) with the least
+ * residual 2-norm. Takes at most n steps (K_n is the whole space) and stops
+ * early only on an exact breakdown (h_{j+1,j} == 0), where d is exact. FP32 mode: A's entries rounded to float and every
+ * operation in float (emulated by or_fl). */
+void or_gmres(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *rhs,
+              int m, int prec, double *d) {
+  const int ld = m + 1;
+  double *V = (double *)calloc((size_t)(m + 1) * (n > 0 ? n : 1), sizeof(double));
+  double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+  double *H = (double *)calloc((size_t)ld * (m > 0 ? m : 1), sizeof(double)); /* H[i + j*ld] */
+  double *cs = (double *)calloc(m > 0 ? m : 1, sizeof(double));
+  double *sn = (double *)calloc(m > 0 ? m : 1, sizeof(double));
+  double *g = (double *)calloc(m + 1, sizeof(double));
+  double *y = (double *)calloc(m > 0 ? m : 1, sizeof(double));
+  for (int i = 0; i < n; ++i) d[i] = 0.0;
+  double beta2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double ri = or_fl(prec, rhs[i]);
+    beta2 = or_fl(prec, beta2 + or_fl(prec, ri * ri));
+  }
+  double beta = or_fl(prec, sqrt(beta2));
+  int k = 0;
+  if (m > n) m = n; /* K_n is already the whole space */
+  if (beta > 0.0) {
+    for (int i = 0; i < n; ++i) V[i] = or_fl(prec, or_fl(prec, rhs[i]) / beta);
+    g[0] = beta;
+    for (int j = 0; j < m; ++j) {
+      const double *vj = V + (size_t)j * n;
+      for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e)
+          s = or_fl(prec, s + or_fl(prec, or_fl(prec, val[e]) * vj[ci[e]]));
+        w[i] = s;
+      }
+      for (int q = 0; q <= j; ++q) {
+        const double *vq = V + (size_t)q * n;
+        double h = 0.0;
+        for (int i = 0; i < n; ++i) h = or_fl(prec, h + or_fl(prec, w[i] * vq[i]));
+        H[q + j * ld] = h;
+        for (int i = 0; i < n; ++i) w[i] = or_fl(prec, w[i] - or_fl(prec, h * vq[i]));
+      }
+      double hn2 = 0.0;
+      for (int i = 0; i < n; ++i) hn2 = or_fl(prec, hn2 + or_fl(prec, w[i] * w[i]));
+      const double hn = or_fl(prec, sqrt(hn2));
+      H[j + 1 + j * ld] = hn;
+      /* earlier rotations on column j, then the one that zeroes h_{j+1,j} */
+      for (int q = 0; q < j; ++q) {
+        const double a = H[q + j * ld], b = H[q + 1 + j * ld];
+        H[q + j * ld] = or_fl(prec, or_fl(prec, cs[q] * a) + or_fl(prec, sn[q] * b));
+        H[q + 1 + j * ld] = or_fl(prec, or_fl(prec, cs[q] * b) - or_fl(prec, sn[q] * a));
+      }
+      const double a = H[j + j * ld];
+      const double den = or_fl(prec, sqrt(or_fl(prec, or_fl(prec, a * a) + or_fl(prec, hn * hn))));
+      if (!(den > 0.0)) break; /* singular on the Krylov space: keep k steps */
+      cs[j] = or_fl(prec, a / den);
+      sn[j] = or_fl(prec, hn / den);
+      H[j + j * ld] = den;
+      H[j + 1 + j * ld] = 0.0;
+      g[j + 1] = -or_fl(prec, sn[j] * g[j]);
+      g[j] = or_fl(prec, cs[j] * g[j]);
+      k = j + 1;
+      if (hn == 0.0) break; /* exact breakdown: the Krylov space is invariant */
+      double *vn = V + (size_t)(j + 1) * n;
+      for (int i = 0; i < n; ++i) vn[i] = or_fl(prec, w[i] / hn);
+    }
+    for (int q = k - 1; q >= 0; --q) {
+      double s = g[q];
+      for (int t = q + 1; t < k; ++t) s = or_fl(prec, s - or_fl(prec, H[q + t * ld] * y[t]));
+      y[q] = or_fl(prec, s / H[q + q * ld]);
+    }
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s = or_fl(prec, s + or_fl(prec, y[q] * V[(size_t)q * n + i]));
+      d[i] = s;
+    }
+  }
+  free(V); free(w); free(H); free(cs); free(sn); free(g); free(y);
 }
 
 static int or_find(const int32_t *rp, const int32_t *ci, int row, int col) {
@@ -555,7 +714,7 @@ typedef struct {
   int32_t *lci;
   double *lval;
   int w;           /* half bandwidth of A_p */
-  double *band;    /* Cholesky factor, band layout */
+  double *band;    /* Cholesky factor (or LU factors, width 2w+1), band layout */
   double *lu;      /* ILU(0) factors on the pattern of A_p */
 } or_sub;
 
@@ -615,6 +774,12 @@ static int or_sub_setup(int n, const int32_t *rp, const int32_t *ci, const doubl
       for (int k = s->lrp[t]; k < s->lrp[t + 1]; ++k)
         if (s->lci[k] <= t) BAND(s->band, w, t, s->lci[k]) = s->lval[k];
     rc = or_band_cholesky(no, w, s->band);
+  } else if (kind == OR_BANDLU) {
+    size_t cnt = (size_t)(no > 0 ? no : 1) * (size_t)(2 * w + 1);
+    s->band = (double *)calloc(cnt, sizeof(double));
+    for (int t = 0; t < no; ++t)
+      for (int k = s->lrp[t]; k < s->lrp[t + 1]; ++k) BANDG(s->band, w, t, s->lci[k]) = s->lval[k];
+    rc = or_band_lu(no, w, s->band);
   } else if (kind == OR_ILU0_CG) {
     s->lu = (double *)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
     rc = or_ilu0(no, s->lrp, s->lci, s->lval, s->lu);
@@ -622,14 +787,18 @@ static int or_sub_setup(int n, const int32_t *rp, const int32_t *ci, const doubl
   return rc;
 }
 
-/* delta = A_p^{-1} rhs (exactly, up to rounding) or m steps of (P)CG. */
+/* delta = A_p^{-1} rhs (exactly, up to rounding) or m steps of (P)CG / GMRES. */
 static void or_sub_solve(const or_sub *s, int kind, int prec, int m, double *rhs_delta) {
   if (kind == OR_BANDCHOL) {
     if (prec == OR_FP64) or_band_solve(s->no, s->w, s->band, rhs_delta);
     else or_band_solve_lowp(s->no, s->w, s->band, prec, rhs_delta);
+  } else if (kind == OR_BANDLU) {
+    if (prec == OR_FP64) or_band_lu_solve(s->no, s->w, s->band, rhs_delta);
+    else or_band_lu_solve_lowp(s->no, s->w, s->band, prec, rhs_delta);
   } else {
     double *d = (double *)malloc(sizeof(double) * (s->no > 0 ? s->no : 1));
     if (kind == OR_CG) or_cg(s->no, s->lrp, s->lci, s->lval, rhs_delta, m, prec, d);
+    else if (kind == OR_GMRES) or_gmres(s->no, s->lrp, s->lci, s->lval, rhs_delta, m, prec, d);
     else or_pcg_ilu0(s->no, s->lrp, s->lci, s->lval, s->lu, rhs_delta, m, prec, d);
     memcpy(rhs_delta, d, sizeof(double) * s->no);
     free(d);
@@ -645,8 +814,8 @@ int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, 
                 const int32_t *part, int P, int gamma, int kind, int prec, int m, double tol,
                 int max_iter, int nthreads, double *x, double *hist, int32_t *iters) {
   if (n <= 0 || P <= 0 || gamma < 0 || max_iter < 0) return OR_EINVAL;
-  if (kind < OR_BANDCHOL || kind > OR_ILU0_CG || prec < OR_FP64 || prec > OR_BF16) return OR_EINVAL;
-  if (prec == OR_BF16 && kind != OR_BANDCHOL) return OR_EINVAL;
+  if (kind < OR_BANDCHOL || kind > OR_GMRES || prec < OR_FP64 || prec > OR_BF16) return OR_EINVAL;
+  if (prec == OR_BF16 && kind != OR_BANDCHOL && kind != OR_BANDLU) return OR_EINVAL;
   for (int i = 0; i < n; ++i)
     if (part[i] < 0 || part[i] >= P) return OR_EINVAL;
   or_sub *subs = (or_sub *)calloc(P, sizeof(or_sub));

@@ -12,7 +12,8 @@
  * interface, red points of Fig. 1). Local unknowns are Omega_p in ascending
  * global order.
  *
- * Return codes: 0 ok, 1 invalid argument, 3 matrix not SPD, 4 no convergence.
+ * Return codes: 0 ok, 1 invalid argument, 3 local factorisation broke down
+ * (Cholesky: not SPD; LU: zero pivot), 4 no convergence.
  */
 #ifndef RAS_ORACLE_H
 #define RAS_ORACLE_H
@@ -27,6 +28,8 @@
 #define OR_BANDCHOL 0
 #define OR_CG 1
 #define OR_ILU0_CG 2
+#define OR_BANDLU 3 /* general matrices */
+#define OR_GMRES 4  /* general matrices */
 #define OR_FP64 0
 #define OR_FP32 1
 #define OR_BF16 2
@@ -53,12 +56,24 @@ void or_band_solve(int n, int w, const double *L, double *x);
 /* Same with factors rounded to `prec` (OR_FP32 / OR_BF16) and FP32 arithmetic. */
 void or_band_solve_lowp(int n, int w, const double *L, int prec, double *x);
 
+/* Banded LU without pivoting (general A_p with half-bandwidth w).
+ * band[i*(2w+1)+t] holds A[i][i-w+t] (t = 0..2w); in place -> unit lower L
+ * below the diagonal, U on and above it. */
+int or_band_lu(int n, int w, double *band);
+/* Solve L U x = rhs in place (FP64), and with rounded factors in FP32. */
+void or_band_lu_solve(int n, int w, const double *LU, double *x);
+void or_band_lu_solve_lowp(int n, int w, const double *LU, int prec, double *x);
+
 /* Dense LU with partial pivoting: solves A x = b in place (A overwritten). */
 int or_dense_lu_solve(int n, double *A, double *b);
 
 /* m iterations of textbook CG on A d = rhs from d = 0 (FP64 or FP32 arithmetic). */
 void or_cg(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *rhs,
            int m, int prec, double *d);
+/* m steps of GMRES (one cycle, Arnoldi with modified Gram-Schmidt, Givens
+ * rotations) on A d = rhs from d = 0, FP64 or FP32 arithmetic. */
+void or_gmres(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *rhs,
+              int m, int prec, double *d);
 /* ILU(0) on the CSR pattern (IKJ order). lu has the pattern of A. */
 int or_ilu0(int n, const int32_t *rp, const int32_t *ci, const double *val, double *lu);
 /* m iterations of CG preconditioned by the ILU(0) factors, from d = 0. */

@@ -3,7 +3,8 @@
 This package builds the linear systems Ax = b that both the CUDA path and the
 CPU oracle consume: the 2D/3D Poisson stencils of the experimental section
 (Sec. 4.1: 5-point stencil S = {-1,-1,4,-1,-1}), a variable-coefficient 2D
-diffusion operator with a log-normal random coefficient, uniform random
+diffusion operator with a log-normal random coefficient, a nonsymmetric
+upwind convection-diffusion operator, uniform random
 right-hand sides and the discrete eigenvector right-hand side.
 
 It holds none of the Schwarz method's arithmetic (no partitioning, overlap,
@@ -16,6 +17,8 @@ from .generators import (  # noqa: F401
     poisson2d,
     poisson3d,
     diffusion2d,
+    convdiff2d,
+    rhs_eigen_convdiff2d,
     grf_coefficient,
     rhs_uniform,
     rhs_eigen2d,

@@ -161,6 +161,58 @@ def diffusion2d(N: int, k: np.ndarray) -> CSR:
     return _assemble(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
+def convdiff2d(N: int, bx: float, by: float) -> CSR:
+    """Upwind convection-diffusion -Laplace(u) + beta . grad(u) on N x N
+    interior nodes, unscaled (a nonsymmetric M-matrix).
+
+    bx, by are the velocity components times the mesh width h. With first-order
+    upwinding the row of node (x, y) is (4 + |bx| + |by|) u - (1 + max(bx, 0))
+    u_west - (1 + max(-bx, 0)) u_east - (1 + max(by, 0)) u_south
+    - (1 + max(-by, 0)) u_north; couplings to the Dirichlet boundary are
+    dropped as for the Poisson matrix. bx = by = 0 gives poisson2d(N); the
+    transpose of convdiff2d(N, bx, by) is convdiff2d(N, -bx, -by).
+    """
+    n = N * N
+    idx = np.arange(n).reshape(N, N)
+    rows = [np.arange(n)]
+    cols = [np.arange(n)]
+    vals = [np.full(n, 4.0 + abs(bx) + abs(by))]
+    # (lower node, upper node, coefficient of the upper row on the lower node,
+    #  coefficient of the lower row on the upper node)
+    for lo, hi, c_up, c_dn in (
+        (idx[:, :-1].ravel(), idx[:, 1:].ravel(), -1.0 - max(bx, 0.0), -1.0 - max(-bx, 0.0)),
+        (idx[:-1, :].ravel(), idx[1:, :].ravel(), -1.0 - max(by, 0.0), -1.0 - max(-by, 0.0)),
+    ):
+        rows += [hi, lo]
+        cols += [lo, hi]
+        vals += [np.full(hi.size, c_up), np.full(lo.size, c_dn)]
+    return _assemble(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def rhs_eigen_convdiff2d(N: int, bx: float, by: float):
+    """Closed-form eigenvector right-hand side for convdiff2d(N, bx, by).
+
+    The matrix is I (x) T_x + T_y (x) I with tridiagonal Toeplitz T = tridiag(s,
+    d, t) per direction (s: coefficient on the lower neighbour, t: on the upper
+    one, d = 2 + |b|). Its eigenvector of lowest frequency is v_j = (s/t)^(j/2)
+    sin(j pi h), j = 1..N, h = 1/(N+1), with eigenvalue d - 2 sqrt(s t) cos(pi h).
+    Returns (b, u, lam) with u the 2D product vector and b = lam u.
+    """
+    h = 1.0 / (N + 1)
+    j = np.arange(1, N + 1)
+
+    def mode(bd):
+        s, t, d = -1.0 - max(bd, 0.0), -1.0 - max(-bd, 0.0), 2.0 + abs(bd)
+        v = (s / t) ** (j / 2.0) * np.sin(j * np.pi * h)
+        return v, d - 2.0 * np.sqrt(s * t) * np.cos(np.pi * h)
+
+    vx, lx = mode(bx)
+    vy, ly = mode(by)
+    u = np.outer(vy, vx).ravel()
+    lam = lx + ly
+    return lam * u, u, lam
+
+
 def grf_coefficient(N: int, seed: int, sigma: float = 1.0, ell: float = 1.0 / 32.0) -> np.ndarray:
     """k = exp(sigma * g) on the N x N interior nodes, g a unit Gaussian field.
 

@@ -314,6 +314,165 @@ def test_band_solve_low_precision_error_bound(prec, eps):
         assert np.array_equal(x, y.astype(np.float64))
 
 
+def _gband_of(S, w):
+    n = S.shape[0]
+    band = np.zeros((n, 2 * w + 1))
+    for i in range(n):
+        for j in range(max(0, i - w), min(n, i + w + 1)):
+            band[i, j - i + w] = S[i, j]
+    return band
+
+
+def _gunband(F, w):
+    """(unit lower L, upper U) from the banded LU factors."""
+    n = F.shape[0]
+    L, U = np.eye(n), np.zeros((n, n))
+    for i in range(n):
+        for j in range(max(0, i - w), min(n, i + w + 1)):
+            if j < i:
+                L[i, j] = F[i, j - i + w]
+            else:
+                U[i, j] = F[i, j - i + w]
+    return L, U
+
+
+@pytest.mark.parametrize("N,bx,by", [(3, 0.5, 0.5), (6, 1.5, -0.7), (10, -3.0, 2.0)])
+def test_band_lu_vs_scipy(N, bx, by):
+    # the convection-diffusion matrix is column diagonally dominant, so
+    # Gaussian elimination with partial pivoting swaps no rows (Golub & Van
+    # Loan, Thm. 3.4.3) and scipy's P L U has P = I with the same L and U
+    import scipy.linalg as sl
+
+    A = problems.convdiff2d(N, bx, by)
+    S = dense(A)
+    F = oracle.band_lu(_gband_of(S, N), N)
+    L, U = _gunband(F, N)
+    Pm, L2, U2 = sl.lu(S)
+    assert np.array_equal(Pm, np.eye(A.n))
+    assert np.allclose(L, L2, rtol=1e-12, atol=1e-14) and np.allclose(U, U2, rtol=1e-12, atol=1e-13)
+    assert np.linalg.norm(L @ U - S) <= 1e-14 * np.linalg.norm(S) * 10
+    rhs = problems.rhs_uniform(A.n, 5)
+    x = oracle.band_lu_solve(F, N, rhs)
+    xs = np.linalg.solve(S, rhs)
+    assert np.linalg.norm(x - xs) <= 1e-12 * np.linalg.norm(xs)
+
+
+def test_band_lu_of_spd_matches_cholesky():
+    # for SPD A: L_lu = L_c diag(L_c)^-1 and U = diag(L_c) L_c^T
+    N = 7
+    A = problems.diffusion2d(N, problems.grf_coefficient(N, 3))
+    S = dense(A)
+    L, U = _gunband(oracle.band_lu(_gband_of(S, N), N), N)
+    Lc = np.linalg.cholesky(S)
+    Dc = np.diag(np.diag(Lc))
+    assert np.allclose(L, Lc @ np.linalg.inv(Dc), rtol=1e-12, atol=1e-14)
+    assert np.allclose(U, Dc @ Lc.T, rtol=1e-12, atol=1e-13)
+
+
+def test_band_lu_zero_pivot():
+    S = np.array([[0.0, 1.0], [1.0, 0.0]])
+    with pytest.raises(oracle.OracleError):
+        oracle.band_lu(_gband_of(S, 1), 1)
+    # a zero pivot that appears only after elimination
+    S = np.array([[1.0, 1.0, 0.0], [1.0, 1.0, 1.0], [0.0, 1.0, 1.0]])
+    with pytest.raises(oracle.OracleError):
+        oracle.band_lu(_gband_of(S, 1), 1)
+
+
+@pytest.mark.parametrize("prec,eps", [(oracle.FP32, 2.0 ** -24), (oracle.BF16, 2.0 ** -9)])
+def test_band_lu_solve_low_precision_error_bound(prec, eps):
+    N = 12
+    A = problems.convdiff2d(N, 0.8, -0.4)
+    S = dense(A)
+    F = oracle.band_lu(_gband_of(S, N), N)
+    rhs = problems.rhs_uniform(A.n, 6)
+    x = oracle.band_lu_solve(F, N, rhs, prec)
+    xs = np.linalg.solve(S, rhs)
+    kappa = np.linalg.cond(S)
+    err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    assert err <= 4 * kappa * (N + 1) * eps
+    assert err >= 1e-2 * eps  # really computed in reduced precision
+
+
+# ---------------------------------------------------------------- GMRES
+
+def _krylov_lsq(S, r, m):
+    """Brute force: the d in K_m(S, r) minimising ||r - S d||, by an
+    orthonormal basis of the Krylov matrix (numpy QR) and least squares."""
+    K = np.empty((r.size, m))
+    v = r.copy()
+    for j in range(m):
+        K[:, j] = v / np.linalg.norm(v)
+        v = S @ K[:, j]
+    Q, _ = np.linalg.qr(K)
+    c, *_ = np.linalg.lstsq(S @ Q, r, rcond=None)
+    return Q @ c
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 6])
+def test_gmres_is_krylov_least_squares(m):
+    A = problems.convdiff2d(7, 1.3, -0.6)
+    S = dense(A)
+    r = problems.rhs_uniform(A.n, 8)
+    d = oracle.gmres(A, r, m)
+    dk = _krylov_lsq(S, r, m)
+    assert np.linalg.norm(d - dk) <= 1e-10 * np.linalg.norm(dk)
+    if m == 1:
+        # one step: d = (r.Ar / |Ar|^2) r
+        Ar = S @ r
+        assert np.allclose(d, (r @ Ar) / (Ar @ Ar) * r, rtol=1e-13, atol=0)
+
+
+def test_gmres_full_space_is_direct_solve():
+    A = problems.convdiff2d(6, -0.9, 0.4)
+    S = dense(A)
+    r = problems.rhs_uniform(A.n, 9)
+    xs = np.linalg.solve(S, r)
+    for m in (A.n, A.n + 10):  # more steps than unknowns: the same n steps
+        d = oracle.gmres(A, r, m)
+        assert np.linalg.norm(d - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_gmres_residual_monotone_and_below_cg_on_spd():
+    A = problems.convdiff2d(12, 0.7, 0.2)
+    S = dense(A)
+    r = problems.rhs_uniform(A.n, 10)
+    res = [np.linalg.norm(r - S @ oracle.gmres(A, r, m)) for m in range(1, 25)]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res, res[1:]))
+    assert res[-1] < 1e-2 * np.linalg.norm(r)
+    # SPD: GMRES minimises the residual 2-norm over the same Krylov space as CG
+    P2 = problems.poisson2d(12)
+    S2 = dense(P2)
+    for m in (3, 8, 15):
+        rg = np.linalg.norm(r - S2 @ oracle.gmres(P2, r, m))
+        rc = np.linalg.norm(r - S2 @ oracle.cg(P2, r, m))
+        assert rg <= rc * (1 + 1e-10)
+
+
+def test_gmres_exact_breakdown_and_zero_rhs():
+    # diagonal A, rhs = e_2: A v_1 is parallel to v_1, h_21 = 0 exactly
+    n = 5
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    D = problems.CSR(n, rp, ci, np.array([2.0, 3.0, 5.0, 7.0, 11.0]))
+    r = np.zeros(n)
+    r[2] = 4.0
+    for prec in (oracle.FP64, oracle.FP32):
+        d = oracle.gmres(D, r, 20, prec)
+        assert np.array_equal(d, np.array([0.0, 0.0, 0.8, 0.0, 0.0], dtype=np.float32).astype(np.float64)
+                              if prec == oracle.FP32 else np.array([0.0, 0.0, 0.8, 0.0, 0.0]))
+    assert np.array_equal(oracle.gmres(D, np.zeros(n), 5), np.zeros(n))
+
+
+def test_gmres_fp32_within_rounding():
+    A = problems.convdiff2d(16, 0.5, 0.5)
+    r = problems.rhs_uniform(A.n, 11)
+    d64 = oracle.gmres(A, r, 20)
+    d32 = oracle.gmres(A, r, 20, oracle.FP32)
+    err = np.linalg.norm(d32 - d64) / np.linalg.norm(d64)
+    assert 1e-9 < err < 1e-4  # really FP32, and only its rounding
+
+
 def test_dense_lu_vs_numpy():
     rng = np.random.default_rng(1)
     M = rng.standard_normal((40, 40))

@@ -236,3 +236,92 @@ def test_invalid_inputs():
         oracle.ras_sync(A, b, np.zeros(16, np.int32), 1, -1)
     with pytest.raises(oracle.OracleError):
         oracle.ras_sync(A, b, np.zeros(16, np.int32), 1, 1, kind=oracle.CG, prec=oracle.BF16)
+    with pytest.raises(oracle.OracleError):
+        oracle.ras_sync(A, b, np.zeros(16, np.int32), 1, 1, kind=oracle.GMRES, prec=oracle.BF16)
+    with pytest.raises(oracle.OracleError):
+        oracle.ras_sync(A, b, np.zeros(16, np.int32), 1, 1, kind=5)
+
+
+# ---------------------------------------------------------------- nonsymmetric systems (Sec. 4.1:
+# a generic system with LU or GMRES local solves)
+
+def test_single_subdomain_nonsymmetric_is_direct_solve():
+    A = problems.convdiff2d(16, 1.0, -0.5)
+    b = problems.rhs_uniform(A.n, 1)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    for kind, m in ((oracle.BANDLU, 1), (oracle.GMRES, A.n)):
+        x, it, hist = oracle.ras_sync(A, b, np.zeros(A.n, np.int32), 1, 2, kind=kind, m=m, tol=1e-8)
+        assert it == 1 and hist[1] < 1e-12
+        assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("kind", [oracle.BANDLU, oracle.GMRES])
+def test_zero_overlap_nonsymmetric_is_block_jacobi(kind):
+    N = 12
+    A = problems.convdiff2d(N, 0.6, 1.1)
+    S = dense(A)
+    b = problems.rhs_uniform(A.n, 2)
+    part = oracle.partition_regular2d(N, N, 3, 2)
+    for k in (1, 2, 7):
+        # GMRES over the whole local space (24 rows) is an exact local solve
+        x, _ = iterate(A, b, part, 6, 0, k, kind=kind, m=24)
+        xj = block_jacobi(S, b, part, 6, k)
+        assert np.linalg.norm(x - xj) <= 1e-11 * max(np.linalg.norm(xj), 1.0)
+
+
+@pytest.mark.parametrize("N,px,py,gamma,bx,by", [(6, 2, 2, 1, 0.8, -0.3), (8, 2, 2, 2, -2.0, 1.0),
+                                                 (7, 3, 1, 1, 4.0, 0.0)])
+def test_iteration_matrix_nonsymmetric(N, px, py, gamma, bx, by):
+    # RAS on an M-matrix converges (rho(T) < 1 for a nonsymmetric M-matrix too)
+    A = problems.convdiff2d(N, bx, by)
+    S = dense(A)
+    b = problems.rhs_uniform(A.n, 3)
+    P = px * py
+    part = oracle.partition_regular2d(N, N, px, py)
+    T, M = ras_operators(S, part, P, gamma, A)
+    assert np.max(np.abs(np.linalg.eigvals(T))) < 1.0
+    xk = np.zeros(A.n)
+    for k in range(1, 6):
+        xk = T @ xk + M @ b
+        x, _ = iterate(A, b, part, P, gamma, k, kind=oracle.BANDLU)
+        assert np.linalg.norm(x - xk) <= 1e-12 * np.linalg.norm(xk)
+
+
+def test_nonsymmetric_converges_to_direct_solution():
+    N = 40
+    A = problems.convdiff2d(N, 1.5, -0.8)
+    b = problems.rhs_uniform(A.n, 4)
+    part = oracle.partition_regular2d(N, N, 2, 2)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    its = {}
+    for kind, prec, m in [(oracle.BANDLU, oracle.FP64, 1), (oracle.BANDLU, oracle.FP32, 1),
+                          (oracle.BANDLU, oracle.BF16, 1), (oracle.GMRES, oracle.FP64, 20),
+                          (oracle.GMRES, oracle.FP32, 20)]:
+        x, it, hist = oracle.ras_sync(A, b, part, 4, 2, kind=kind, prec=prec, m=m, tol=1e-9)
+        assert hist[-1] < 1e-9
+        assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-7
+        its[(kind, prec)] = it
+    # FP32 factors: the correction form keeps the FP64 iteration count
+    assert abs(its[(oracle.BANDLU, oracle.FP32)] - its[(oracle.BANDLU, oracle.FP64)]) <= 2
+
+
+def test_gmres_with_full_local_space_equals_lu():
+    N = 14
+    A = problems.convdiff2d(N, -0.7, 0.9)
+    b = problems.rhs_uniform(A.n, 9)
+    part = oracle.partition_regular2d(N, N, 2, 2)
+    xd, _ = iterate(A, b, part, 4, 1, 6, kind=oracle.BANDLU)
+    xg, _ = iterate(A, b, part, 4, 1, 6, kind=oracle.GMRES, m=200)
+    assert np.linalg.norm(xd - xg) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_convdiff_eigenvector_rhs_error_bound():
+    # b = lam u with u the closed-form lowest mode: x* = u exactly
+    N = 48
+    A = problems.convdiff2d(N, 0.5, 0.5)
+    b, u, lam = problems.rhs_eigen_convdiff2d(N, 0.5, 0.5)
+    part = oracle.partition_regular2d(N, N, 2, 2)
+    x, it, hist = oracle.ras_sync(A, b, part, 4, 2, kind=oracle.BANDLU, tol=1e-10)
+    kappa = np.linalg.cond(dense(A))
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= kappa * hist[-1]
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= 1e-7

@@ -116,3 +116,41 @@ def test_grf_statistics():
     c = np.mean(g[:, :-lag] * g[:, lag:]) / g.var()
     assert 0.45 < c < 0.75
     assert np.array_equal(g, np.log(problems.grf_coefficient(N, seed=4)))
+
+
+@pytest.mark.parametrize("N,bx,by", [(5, 0.5, -0.3), (9, -1.2, 0.0), (16, 2.0, 3.0)])
+def test_convdiff_structure(N, bx, by):
+    A = problems.convdiff2d(N, bx, by)
+    S = A.to_scipy().toarray()
+    # flow reversal is the transpose; no convection is the Poisson matrix
+    assert np.array_equal(S.T, problems.convdiff2d(N, -bx, -by).to_scipy().toarray())
+    assert np.array_equal(problems.convdiff2d(N, 0.0, 0.0).to_scipy().toarray(),
+                          problems.poisson2d(N).to_scipy().toarray())
+    # M-matrix rows: positive diagonal, non-positive off-diagonal, zero row sum
+    # away from the boundary (upwinding adds |b| to the diagonal and to one side)
+    assert np.all(np.diag(S) == 4.0 + abs(bx) + abs(by))
+    off = S - np.diag(np.diag(S))
+    assert np.all(off <= 0.0)
+    rs = S.sum(1).reshape(N, N)
+    if N > 2:
+        assert np.allclose(rs[1:-1, 1:-1], 0.0, atol=1e-14)
+    assert np.all(rs >= -1e-14)
+    # west neighbour of (x, y) carries -(1 + max(bx, 0))
+    i = 1 * N + 1 if N > 2 else 1
+    assert S[i, i - 1] == -1.0 - max(bx, 0.0) and S[i, i + 1] == -1.0 - max(-bx, 0.0)
+    if bx or by:
+        assert not np.array_equal(S, S.T)
+
+
+@pytest.mark.parametrize("N,bx,by", [(8, 0.5, -0.3), (33, 1.5, 0.25), (20, 0.0, 0.0)])
+def test_convdiff_eigenvector_closed_form(N, bx, by):
+    A = problems.convdiff2d(N, bx, by)
+    b, u, lam = problems.rhs_eigen_convdiff2d(N, bx, by)
+    assert np.linalg.norm(A.matvec(u) - lam * u) <= 1e-13 * np.linalg.norm(u) * lam
+    assert np.array_equal(b, lam * u)
+    if bx == 0.0 and by == 0.0:
+        b2, u2, lam2 = problems.rhs_eigen2d(N)
+        assert np.allclose(u, u2, rtol=1e-14) and abs(lam - lam2) <= 1e-15
+    # the smallest eigenvalue of the nonsymmetric matrix (all eigenvalues are real)
+    ev = np.linalg.eigvals(A.to_scipy().toarray())
+    assert abs(np.min(ev.real) - lam) <= 1e-10 and np.max(np.abs(ev.imag)) <= 1e-8
