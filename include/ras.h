@@ -1,8 +1,11 @@
 /*
  * ras.h - C ABI of the GB300 asynchronous Restricted Additive Schwarz solver.
  *
- * The library solves A x = b (Eq. 1) for a sparse symmetric positive definite
- * A by Restricted Additive Schwarz (Sec. 2.1): the unknowns are partitioned
+ * The library solves A x = b (Eq. 1) for a sparse matrix A (symmetric positive
+ * definite for the Cholesky / CG / ILU(0)-PCG local solvers; any matrix with
+ * nonsingular, pivot-free local blocks for the LU / GMRES local solvers of
+ * the generic systems of Sec. 4.1) by Restricted Additive Schwarz (Sec. 2.1):
+ * the unknowns are partitioned
  * into subdomains (Sec. 3.2.1), each subdomain is grown by `overlap` layers of
  * graph neighbours (Fig. 1), every subdomain solves its local problem on the
  * overlapped set and keeps only the values it owns. Subdomains run as CTAs of
@@ -40,7 +43,8 @@ typedef enum {
   RAS_OK = 0,
   RAS_EINVAL = 1,   /* invalid argument (sizes, indices, pointers, options) */
   RAS_ENOMEM = 2,   /* host or device allocation failed */
-  RAS_ENOTSPD = 3,  /* a local factorisation met a non-positive pivot, or a row of A_p
+  RAS_ENOTSPD = 3,  /* a local factorisation broke down: a non-positive pivot
+                       (Cholesky, ILU(0)) or a zero pivot (LU), or a row of A_p
                        has no positive diagonal entry (local CG) */
   RAS_ENOCONV = 4,  /* max updates / restarts reached; x holds the last iterate */
   RAS_ETIMEOUT = 5, /* a device-side wait exceeded its limit; x is undefined */
@@ -60,13 +64,25 @@ typedef enum { RAS_SYNC = 0, RAS_ASYNC = 1, RAS_ASYNC_DECENTRAL = 2 } ras_mode;
 
 /* Local solvers (Sec. 3.3.1): a banded Cholesky factorisation computed once
  * in ras_setup with triangular solves in every update, or `inner_iters` steps
- * of CG / ILU(0)-preconditioned CG from a zero initial guess. */
-typedef enum { RAS_LOCAL_BANDCHOL = 0, RAS_LOCAL_CG = 1, RAS_LOCAL_ILU0_CG = 2 } ras_local_kind;
+ * of CG / ILU(0)-preconditioned CG from a zero initial guess. For general
+ * (nonsymmetric) systems (Sec. 4.1): RAS_LOCAL_BANDLU, a banded LU
+ * factorisation without pivoting (local half-bandwidth <= 112, else
+ * RAS_ENOTSUP; a zero pivot gives RAS_ENOTSPD), applied like the Cholesky
+ * factors; RAS_LOCAL_GMRES, `inner_iters` (1..32) steps of one GMRES cycle from
+ * a zero initial guess (at most |Omega_p| steps). Banded Cholesky accepts
+ * local half-bandwidths up to 160. */
+typedef enum {
+  RAS_LOCAL_BANDCHOL = 0,
+  RAS_LOCAL_CG = 1,
+  RAS_LOCAL_ILU0_CG = 2,
+  RAS_LOCAL_BANDLU = 3,
+  RAS_LOCAL_GMRES = 4
+} ras_local_kind;
 
 /* Precision of the local solve. The outer residual, the update of x and the
  * convergence tests are always FP64. RAS_FP32: factors / local matrix stored
  * and used in FP32. RAS_BF16_STORE: band factors stored in bfloat16, applied
- * in FP32 arithmetic (RAS_LOCAL_BANDCHOL only). */
+ * in FP32 arithmetic (the banded solvers only). */
 typedef enum { RAS_FP64 = 0, RAS_FP32 = 1, RAS_BF16_STORE = 2 } ras_prec;
 
 /* Sparse matrix in CSR form. HOST pointers. row_ptr[n+1] (row_ptr[0] = 0,
@@ -84,7 +100,8 @@ typedef struct {
 typedef struct {
   int32_t kind;        /* ras_local_kind */
   int32_t prec;        /* ras_prec */
-  int32_t inner_iters; /* CG / PCG steps per local solve (ignored for BANDCHOL) */
+  int32_t inner_iters; /* CG / PCG / GMRES steps per local solve (ignored by the
+                          banded solvers) */
 } ras_local_solver;
 
 /* Result of one solve. */

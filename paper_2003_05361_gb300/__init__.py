@@ -22,7 +22,7 @@ from . import build as _build
 
 RAS_OK, RAS_EINVAL, RAS_ENOMEM, RAS_ENOTSPD, RAS_ENOCONV, RAS_ETIMEOUT, RAS_ECUDA, RAS_ENOTSUP = range(8)
 RAS_SYNC, RAS_ASYNC, RAS_ASYNC_DECENTRAL = 0, 1, 2
-RAS_LOCAL_BANDCHOL, RAS_LOCAL_CG, RAS_LOCAL_ILU0_CG = 0, 1, 2
+RAS_LOCAL_BANDCHOL, RAS_LOCAL_CG, RAS_LOCAL_ILU0_CG, RAS_LOCAL_BANDLU, RAS_LOCAL_GMRES = 0, 1, 2, 3, 4
 RAS_FP64, RAS_FP32, RAS_BF16_STORE = 0, 1, 2
 
 _lock = threading.Lock()

@@ -172,6 +172,8 @@ struct ras_ctx {
   int32_t *d_ifc = nullptr, *d_ibc = nullptr;  // ILU(0) factors in level order
   void *d_ifv = nullptr, *d_ibv = nullptr, *d_ibd = nullptr;
   int32_t ilu_kl = 0, ilu_ku = 0;
+  void *d_kry = nullptr;  // GMRES Krylov basis scratch
+  int32_t kry_ld = 0;
   int64_t device_bytes = 0;
   // launch state
   LaunchPlan plan;
@@ -549,6 +551,8 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.lev_ptr = c->d_levp;
   s.lev_rows = c->d_levr;
   s.nbr = c->d_nbr;
+  s.kry = c->d_kry;
+  s.kry_ld = c->kry_ld;
   return s;
 }
 
@@ -675,10 +679,12 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   if (!out) return RAS_EINVAL;
   *out = nullptr;
   if (!partition || P <= 0 || overlap < 0 || !lsv) return RAS_EINVAL;
-  if (lsv->kind < RAS_LOCAL_BANDCHOL || lsv->kind > RAS_LOCAL_ILU0_CG) return RAS_EINVAL;
+  if (lsv->kind < RAS_LOCAL_BANDCHOL || lsv->kind > RAS_LOCAL_GMRES) return RAS_EINVAL;
   if (lsv->prec < RAS_FP64 || lsv->prec > RAS_BF16_STORE) return RAS_EINVAL;
-  if (lsv->prec == RAS_BF16_STORE && lsv->kind != RAS_LOCAL_BANDCHOL) return RAS_EINVAL;
-  if (lsv->kind != RAS_LOCAL_BANDCHOL && lsv->inner_iters <= 0) return RAS_EINVAL;
+  const bool banded = lsv->kind == RAS_LOCAL_BANDCHOL || lsv->kind == RAS_LOCAL_BANDLU;
+  if (lsv->prec == RAS_BF16_STORE && !banded) return RAS_EINVAL;
+  if (!banded && lsv->inner_iters <= 0) return RAS_EINVAL;
+  if (lsv->kind == RAS_LOCAL_GMRES && lsv->inner_iters > kMaxGmres) return RAS_EINVAL;
   ras_status st = check_csr(A);
   if (st != RAS_OK) return st;
   const int n = A->n;
@@ -737,20 +743,22 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     rows += d.npad;
     owns += d.n_own;
     nbrs += d.n_nbr;
-    if (kind == RAS_LOCAL_BANDCHOL) {
-      if (mp.w > 160) return RAS_ENOTSUP;
+    if (banded) {
+      if (mp.w > (kind == RAS_LOCAL_BANDLU ? kMaxBandLuW : kMaxBandW)) return RAS_ENOTSUP;
       fac += 2ll * (d.npad / 32) * 32 * (d.W + 32);  // forward and backward records
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
-      c->cost[p] = (double)d.n * K * (m + 1) * (kind == RAS_LOCAL_ILU0_CG ? 3.0 : 1.0);
+      c->cost[p] = kind == RAS_LOCAL_GMRES
+                       ? (double)d.n * (K * (m + 1) + 4.0 * m * (m + 1))  // + CGS2 projections
+                       : (double)d.n * K * (m + 1) * (kind == RAS_LOCAL_ILU0_CG ? 3.0 : 1.0);
     }
     c->maxw = std::max(c->maxw, mp.w);
     npad_max = std::max(npad_max, d.npad);
   }
-  c->plan.Wmax = kind == RAS_LOCAL_BANDCHOL ? Wmax : 0;
+  c->plan.Wmax = banded ? Wmax : 0;
   c->plan.npad_max = npad_max;
-  c->exec_kind = kind;
+  c->exec_kind = banded ? kBand : kind == RAS_LOCAL_GMRES ? kGMRES : kind;
   if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && K <= kMaxEll && npad_max <= kStagedRows &&
       env_int("RAS_CG_STAGE", 1) != 0)
     c->exec_kind = kCGS;
@@ -763,7 +771,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   std::vector<double> lval64, lu64;
   std::vector<double> band;  // FP64 bands for the GPU factorisation
   std::vector<int64_t> band_off(P, 0);
-  if (kind != RAS_LOCAL_BANDCHOL) {
+  const bool lu = kind == RAS_LOCAL_BANDLU;
+  if (!banded) {
     lcol.assign(rows * K, 0);
     lval64.assign(rows * K, 0.0);
     if (kind == RAS_LOCAL_ILU0_CG) lu64.assign(rows * K, 0.0);
@@ -771,7 +780,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     int64_t bsz = 0;
     for (int p = 0; p < P; ++p) {
       band_off[p] = bsz;
-      bsz += (int64_t)c->subs[p].n * (maps[p].w + 1);
+      // Cholesky: lower half (ld = w+1); LU: the whole band (ld = 2w+1)
+      bsz += (int64_t)c->subs[p].n * (lu ? 2 * maps[p].w + 1 : maps[p].w + 1);
     }
     band.assign(bsz, 0.0);
   }
@@ -798,7 +808,9 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         rval[ro * K + (int64_t)k * d.npad + i] = A->val[e];
         const int j = local_index(mp.omega, col);
         if (j < 0) continue;
-        if (kind == RAS_LOCAL_BANDCHOL) {
+        if (lu) {
+          band[band_off[p] + (int64_t)i * (2 * mp.w + 1) + (j - i + mp.w)] = A->val[e];
+        } else if (banded) {
           if (j <= i) band[band_off[p] + (int64_t)i * (mp.w + 1) + (j - i + mp.w)] = A->val[e];
         } else {
           lcol[ro * K + (int64_t)kl * d.npad + i] = j;
@@ -811,7 +823,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         }
       }
       for (; k < K; ++k) rcol[ro * K + (int64_t)k * d.npad + i] = g;  // zero-valued padding
-      if (kind != RAS_LOCAL_BANDCHOL)
+      if (!banded)
         for (; kl < K; ++kl) lcol[ro * K + (int64_t)kl * d.npad + i] = i;
       if (kind == RAS_LOCAL_ILU0_CG) lrp.push_back((int32_t)lci.size());
     }
@@ -819,7 +831,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       gidx[ro + i] = mp.omega[0];
       for (int k = 0; k < K; ++k) {
         rcol[ro * K + (int64_t)k * d.npad + i] = mp.omega[0];
-        if (kind != RAS_LOCAL_BANDCHOL) lcol[ro * K + (int64_t)k * d.npad + i] = i < d.n ? i : 0;
+        if (!banded) lcol[ro * K + (int64_t)k * d.npad + i] = i < d.n ? i : 0;
       }
     }
     for (size_t q = 0; q < mp.nbr.size(); ++q) nbr[d.nbr_off + q] = mp.nbr[q];
@@ -925,7 +937,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   CUDA_TRY(cudaMemsetAsync(c->d_ctl, 0, sizeof(GridCtl), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->d_xalt, 0, sizeof(double) * n, c->stream));
 
-  if (kind == RAS_LOCAL_BANDCHOL) {
+  if (banded) {
     // factorise on the GPU in FP64, then lay out the block records in the storage precision
     double *d_band = nullptr;
     BandJob *d_jobs = nullptr;
@@ -969,8 +981,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     c->bufs.push_back({d_fac, fbytes});
     c->device_bytes += (int64_t)fbytes;
     c->d_fac = d_fac;
-    e = launch_band_chol(d_jobs, P, maxw, d_band, c->d_ctl, c->stream);
-    if (e == cudaSuccess) e = launch_band_layout(prec, d_ljobs, (int)ljobs.size(), d_band, d_fac, c->stream);
+    e = lu ? launch_band_lu(d_jobs, P, maxw, d_band, c->d_ctl, c->stream)
+           : launch_band_chol(d_jobs, P, maxw, d_band, c->d_ctl, c->stream);
+    if (e == cudaSuccess)
+      e = launch_band_layout(prec, lu, d_ljobs, (int)ljobs.size(), d_band, d_fac, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d_band);
@@ -1083,6 +1097,20 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       }
       if ((st = c->upload(c->d_levp, levp_all)) != RAS_OK) return st;
       if ((st = c->upload(c->d_levr, levr_all)) != RAS_OK) return st;
+    }
+    if (kind == RAS_LOCAL_GMRES) {
+      // Krylov basis scratch: m+1 vectors per subdomain in the solve precision
+      c->kry_ld = m + 1;
+      const size_t cnt = (size_t)rows * c->kry_ld;
+      if (prec == RAS_FP64) {
+        double *q = nullptr;
+        if ((st = c->alloc(q, cnt)) != RAS_OK) return st;
+        c->d_kry = q;
+      } else {
+        float *q = nullptr;
+        if ((st = c->alloc(q, cnt)) != RAS_OK) return st;
+        c->d_kry = q;
+      }
     }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
   }
@@ -1536,17 +1564,20 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
   std::vector<Cand> cands;
   const int kind = c->ls.kind, prec = c->ls.prec, m0 = c->ls.inner_iters;
   std::vector<int> ms = {m0};
-  if (tune_inner && kind != RAS_LOCAL_BANDCHOL) {
+  const bool banded = kind == RAS_LOCAL_BANDCHOL || kind == RAS_LOCAL_BANDLU;
+  if (tune_inner && !banded) {
     ms.push_back(std::max(1, m0 / 2));
-    ms.push_back(2 * m0);
+    // GMRES: the Krylov scratch holds at most the set-up step count
+    if (kind != RAS_LOCAL_GMRES) ms.push_back(2 * m0);
   }
   for (int m : ms) {
-    if (kind == RAS_LOCAL_BANDCHOL) {
+    if (banded) {
       cands.push_back({kBand, 128, m});
       cands.push_back({kBand, 256, m});
     } else {
-      cands.push_back({kind, 256, m});
-      cands.push_back({kind, 512, m});
+      const int ek = kind == RAS_LOCAL_GMRES ? kGMRES : kind;
+      cands.push_back({ek, 256, m});
+      cands.push_back({ek, 512, m});
       if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && c->d_lcol16) cands.push_back({kCGS, 512, m});
     }
   }

@@ -10,16 +10,18 @@
 //     entry k of local row i at row_off*K + k*npad + i). It computes
 //     r_p = b[Omega_p] - A[Omega_p, :] x, reading x on Omega_p and E_p;
 //   * the owned-row list own_l (local ids);
-//   * local-solver data: banded-Cholesky block records (fac), or the local matrix A_p
-//     in ELL form with LOCAL columns (lcol/lval) plus ILU(0) factors (luval)
-//     and level schedules.
+//   * local-solver data: banded-Cholesky or banded-LU block records (fac), or the
+//     local matrix A_p in ELL form with LOCAL columns (lcol/lval) plus ILU(0)
+//     factors (luval) and level schedules, or the GMRES Krylov basis scratch.
 #pragma once
 #include <stdint.h>
 
 namespace ras {
 
-enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2,
-                          kCGS = 3 };  // kCGS: CG with A_p staged in shared memory (kernel variant)
+// kernel variants: kBand runs the banded triangular solves of both banded
+// factorisations (Cholesky and LU share the record layout); kCGS is CG with
+// A_p staged in shared memory
+enum LocalKind : int32_t { kBand = 0, kCG = 1, kILU = 2, kCGS = 3, kGMRES = 4 };
 enum Prec : int32_t { kF64 = 0, kF32 = 1, kBF16 = 2 };
 enum Mode : int32_t { kSync = 0, kAsync = 1, kAsyncDecentral = 2 };
 // status codes (mirror ras_status)
@@ -36,6 +38,7 @@ struct SubDesc {
   int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
   int64_t own_off;  // offset into own_l
   int64_t fac_off;  // band: nb forward records, then nb backward records (32 x (W+32) each)
+                    // (forward from L, backward from U = L^T (Cholesky) or U (LU))
   int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
   int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
   int32_t nlev_f;   // ILU: number of forward / backward levels
@@ -122,6 +125,12 @@ struct SysDesc {
   const int32_t *lev_ptr;
   const int32_t *lev_rows;
   const int32_t *nbr;
+  // GMRES: Krylov basis scratch in the local-solve precision, kry_ld vectors
+  // of npad entries per subdomain from row_off * kry_ld (vector q of local
+  // row i at row_off * kry_ld + q * npad + i); kry_ld - 1 bounds the steps
+  void *kry;
+  int32_t kry_ld;
+  int32_t pad2_;
 };
 
 struct Item {
@@ -135,6 +144,10 @@ constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
 constexpr int kMaxEll = 8;      // ELL widths up to this are fully unrolled
 constexpr int kIluHalf = 4;     // ILU(0): strictly lower / upper entries per row kept in registers
 constexpr int kStagedRows = 6144;  // largest subdomain of the staged CG variant
+constexpr int kMaxBandW = 160;     // banded Cholesky: largest half-bandwidth
+constexpr int kMaxBandLuW = 112;   // banded LU: largest half-bandwidth (factorisation window
+                                   // of (w+1) x (2w+1) FP64 values in shared memory)
+constexpr int kMaxGmres = 32;      // GMRES: most Arnoldi steps per local solve
 
 struct GridCtl {
   unsigned int count;  // barrier arrivals

@@ -4,10 +4,13 @@
 //   band_chol_kernel     setup: banded Cholesky A_p = L L^T in FP64, one CTA per
 //                        subdomain, sliding (w+1)x(w+1) window in shared memory
 //                        (direct local solver of Sec. 3.3.1, factorised once).
-//   band_layout_kernel   setup: turns L into the per-block records read by the
-//                        chained triangular solves ([inverse 32x32 diagonal
-//                        block | window operator]), rounded to the storage
-//                        precision (FP64 / FP32 / BF16).
+//   band_lu_kernel       setup: banded LU A_p = L U without pivoting in FP64
+//                        for general (nonsymmetric) systems, sliding
+//                        (w+1)x(2w+1) window (the LU local solver of Sec. 4.1).
+//   band_layout_kernel   setup: turns L and U into the per-block records read
+//                        by the chained triangular solves ([inverse 32x32
+//                        diagonal block | window operator]), rounded to the
+//                        storage precision (FP64 / FP32 / BF16).
 //   ras_init_kernel      per solve: ||b||^2 over Omega_p and O_p, state reset.
 //   ras_sysnorm_kernel   per solve: per-system sums in a fixed order.
 //   ras_main_kernel      the persistent RAS kernel, one CTA per group of
@@ -340,39 +343,115 @@ __global__ void __launch_bounds__(256) band_chol_kernel(const BandJob *jobs, dou
 }
 
 // --------------------------------------------------------------------------
+// setup: banded LU without pivoting (FP64), for general A_p
+// --------------------------------------------------------------------------
+
+// band (row-major, ld = 2w+1): band[i*ld + t] = A[i][i-w+t]; overwritten by
+// the unit lower L (t < w) and U (t >= w). Right-looking: for column j the
+// pivot u_jj, the multipliers l_ij = a_ij / u_jj for i in (j, j+w], then
+// a_ik -= l_ij u_jk on the trailing (w x w) block. Rows j..j+w live in a
+// circular window of shared memory (slot = row mod (w+1)). A zero pivot
+// stops the factorisation with kENOTSPD (no pivoting: the local matrices of
+// an M-matrix, or of any diagonally dominant matrix, never need it).
+__global__ void __launch_bounds__(256) band_lu_kernel(const BandJob *jobs, double *band,
+                                                      GridCtl *ctl) {
+  extern __shared__ __align__(16) double win[];
+  __shared__ double s_piv;
+  __shared__ int s_bad;
+  const BandJob jb = jobs[blockIdx.x];
+  const int n = jb.n, w = jb.w, ld = 2 * w + 1, nw = w + 1;
+  double *B = band + jb.band_off;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int e = tid; e < nw * ld; e += NT) {
+    const int r = e / ld;
+    win[e] = r < n ? B[(int64_t)r * ld + (e % ld)] : 0.0;
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int sj = j % nw;
+    if (j > 0) {
+      // row j-1 is final: write it out, load row j+w into its slot
+      const int sp = (j - 1) % nw;
+      const int rin = j + w;
+      for (int t = tid; t < ld; t += NT) {
+        B[(int64_t)(j - 1) * ld + t] = win[sp * ld + t];
+        win[sp * ld + t] = rin < n ? B[(int64_t)rin * ld + t] : 0.0;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const double u = win[sj * ld + w];
+      if (!(fabs(u) > 0.0)) s_bad = 1;
+      s_piv = u;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double u = s_piv;
+    const int nr = min(w, n - 1 - j);  // rows (and columns) j+1 .. j+nr
+    for (int q = tid; q < nr; q += NT) {
+      const int i = j + 1 + q;
+      win[(i % nw) * ld + (j - i + w)] /= u;
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * nr; e += NT) {
+      const int qi = e / nr, qk = e % nr;
+      const int i = j + 1 + qi, k = j + 1 + qk;
+      const int si = i % nw;
+      win[si * ld + (k - i + w)] -= win[si * ld + (j - i + w)] * win[sj * ld + (k - j + w)];
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) set_error(ctl, kENOTSPD, (unsigned long long)blockIdx.x);
+    return;
+  }
+  if (n > 0) {
+    const int sl = (n - 1) % nw;
+    for (int t = tid; t < ld; t += NT) B[(int64_t)(n - 1) * ld + t] = win[sl * ld + t];
+  }
+}
+
+// --------------------------------------------------------------------------
 // setup: operators of the blocked triangular solves
 // --------------------------------------------------------------------------
 //
 // Rows are grouped in blocks of 32 (K = 0..nb-1; rows >= n are identity rows).
-// With L_KK the diagonal block of the Cholesky factor and W = the local
+// With L_KK the diagonal block of the lower factor and W = the local
 // half-bandwidth w, forward substitution block by block is
 //   y_K = L_KK^{-1} (r_K - L_{K,left} y_left) = t_K - M_K y[32K-W, 32K),
 //   t_K = L_KK^{-1} r_K,  M_K = L_KK^{-1} L[K rows, 32K-W .. 32K)   (32 x W)
-// and backward substitution with U = L^T
+// and backward substitution with the upper factor U
 //   z_K = t'_K - M'_K z[32K+32, 32K+32+W),  t'_K = U_KK^{-1} y_K,
 //   M'_K = U_KK^{-1} U[K rows, 32K+32 .. 32K+32+W)                   (32 x W).
+// Cholesky: L from the band (ld = w+1), U = L^T, so U_KK^{-1} = (L_KK^{-1})^T.
+// LU: unit lower L and U from one band (ld = 2w+1), U_KK inverted on its own.
 // Per subdomain the storage is nb forward records, then nb backward records,
 // each a column-major 32 x (32 + W) matrix (entry (l, j) at j*32 + l):
 //   forward  record K = [ L_KK^{-1} | M_K  ],
-//   backward record K = [ U_KK^{-1} | M'_K ],  U_KK^{-1} = (L_KK^{-1})^T,
+//   backward record K = [ U_KK^{-1} | M'_K ],
 // so that a chain step reads one contiguous record and every one of its
 // 32 + W columns is applied to one broadcast value (the step's own right-hand
 // side for the first 32, a finished window row for the rest).
-template <typename T>
+template <typename T, bool LU>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
   __shared__ double Lkk[32][33];
-  __shared__ double X[32][33];
+  __shared__ double X[32][33];              // L_KK^{-1}
+  __shared__ double Y[LU ? 32 : 1][33];     // U_KK^{-1} (LU)
   const LayoutJob jb = jobs[blockIdx.x];
   const int l = threadIdx.x;
-  const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, nb = jb.nb, ld = w + 1;
+  const int n = jb.n, w = jb.w, W = jb.W, K = jb.K, nb = jb.nb, ld = LU ? 2 * w + 1 : w + 1;
   const double *Bd = band + jb.band_off;
   const int i = 32 * K + l;
+  // entry (r, c) of the band, |c - r| <= w, r < n
+  auto at = [&](int r, int c) -> double { return Bd[(int64_t)r * ld + (c - r + w)]; };
   for (int m = 0; m < 32; ++m) {
     double v = 0.0;
     const int jcol = 32 * K + m;
     if (i < n) {
-      if (m <= l && l - m <= w) v = Bd[(int64_t)i * ld + (jcol - i + w)];
+      if (m < l && l - m <= w) v = at(i, jcol);
+      else if (m == l) v = LU ? 1.0 : at(i, jcol);
     } else if (m == l) {
       v = 1.0;
     }
@@ -397,12 +476,42 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) X[r][m] = col[r];
   }
   __syncwarp();
+  if (LU) {
+    // U_KK (row l, column m >= l), then lane m computes column m of its
+    // inverse by backward substitution
+    for (int m = 0; m < 32; ++m) {
+      double v = 0.0;
+      const int jcol = 32 * K + m;
+      if (i < n) {
+        if (m >= l && m - l <= w && jcol < n) v = at(i, jcol);
+      } else if (m == l) {
+        v = 1.0;
+      }
+      Lkk[l][m] = v;
+    }
+    __syncwarp();
+    const int m = l;
+    double col[32];
+#pragma unroll
+    for (int r = 31; r >= 0; --r) {
+      double s = (r == m) ? 1.0 : 0.0;
+      if (r <= m) {
+        for (int q = r + 1; q <= m; ++q) s -= Lkk[r][q] * col[q];
+        col[r] = s / Lkk[r][r];
+      } else {
+        col[r] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) Y[LU ? r : 0][m] = col[r];
+    __syncwarp();
+  }
   const int64_t rec = (int64_t)32 * (W + 32);
   T *F = fac + jb.fac_off + (int64_t)K * rec;
   T *Bk = fac + jb.fac_off + (int64_t)nb * rec + (int64_t)K * rec;
   for (int m = 0; m < 32; ++m) {
-    F[m * 32 + l] = from_double<T>(X[l][m]);   // L_KK^{-1}[l][m]
-    Bk[m * 32 + l] = from_double<T>(X[m][l]);  // U_KK^{-1}[l][m]
+    F[m * 32 + l] = from_double<T>(X[l][m]);                           // L_KK^{-1}[l][m]
+    Bk[m * 32 + l] = from_double<T>(LU ? Y[LU ? l : 0][m] : X[m][l]);  // U_KK^{-1}[l][m]
   }
   // M_K[l][c] = sum_{m <= l} Linv[l][m] L[32K+m][32K-W+c]
   for (int c = 0; c < W; ++c) {
@@ -411,18 +520,19 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     if (col >= 0)
       for (int m = 0; m <= l; ++m) {
         const int r = 32 * K + m;
-        if (r < n && col >= r - w) s += X[l][m] * Bd[(int64_t)r * ld + (col - r + w)];
+        if (r < n && col >= r - w) s += X[l][m] * at(r, col);
       }
     F[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
   }
-  // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c],  U[a][b] = L[b][a]
+  // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c]
+  // (Cholesky: U[a][b] = L[b][a])
   for (int c = 0; c < W; ++c) {
     const int r = 32 * K + 32 + c;
     double s = 0.0;
     if (r < n)
       for (int m = l; m < 32; ++m) {
         const int col = 32 * K + m;
-        if (col >= r - w) s += X[m][l] * Bd[(int64_t)r * ld + (col - r + w)];
+        if (col >= r - w) s += LU ? Y[LU ? l : 0][m] * at(col, r) : X[m][l] * at(r, col);
       }
     Bk[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
   }
@@ -963,6 +1073,145 @@ __device__ void pcg_solve(const SysDesc &S, const SubDesc &D, int m, CT *r, CT *
   }
 }
 
+// GMRES work area in shared memory (after the four vectors): the Hessenberg
+// matrix (column-major, kMaxGmres+1 rows), the Givens rotations, the
+// least-squares right-hand side g, the projections / solution y, per-warp
+// partial sums of the projections, and two ints.
+template <typename CT, int NT>
+struct GmresSmem {
+  static constexpr int LDH = kMaxGmres + 1;
+  static constexpr int H = 0, CS = H + LDH * kMaxGmres, SN = CS + kMaxGmres, G = SN + kMaxGmres,
+                       Y = G + LDH, PART = Y + LDH, LEN = PART + (NT / 32) * LDH;
+  static constexpr size_t bytes() { return (size_t)LEN * sizeof(CT) + 16; }
+};
+
+// m steps of GMRES on A_p d = r from d = 0, one cycle (Sec. 4.1 names GMRES
+// as the iterative local solver for general systems; the method is Saad &
+// Schultz's). Arnoldi builds the orthonormal basis V (global scratch, L2
+// resident) and the Hessenberg matrix H; Givens rotations reduce H to upper
+// triangular R while carrying ||r|| e_1 along as g; then R y = g and
+// d = V_k y minimises ||r - A_p d|| over the Krylov space. Orthogonalisation
+// is classical Gram-Schmidt applied twice: one block reduction of all j+1
+// projections per pass instead of j+1 dependent ones, and with the second
+// pass as accurate as modified Gram-Schmidt. At most n steps; an exact
+// breakdown (h_{j+1,j} = 0) stops early with the exact solution. Thread t
+// owns rows t, t+NT, ... of every vector, including its rows of V.
+template <typename T, typename CT, int NT>
+__device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict__ lv, int K, int n,
+                            int npad, int m, CT *r, CT *w, CT *v, CT *d, CT *__restrict__ V,
+                            CT *gs, CT *red) {
+  using GS = GmresSmem<CT, NT>;
+  constexpr int LDH = GS::LDH;
+  CT *H = gs + GS::H, *cs = gs + GS::CS, *sn = gs + GS::SN, *g = gs + GS::G, *y = gs + GS::Y,
+     *part = gs + GS::PART;
+  int *flag = reinterpret_cast<int *>(gs + GS::LEN);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int mm = min(m, n);
+  CT b2 = CT(0);
+  for (int i = tid; i < npad; i += NT) {
+    d[i] = CT(0);
+    if (i < n) b2 += r[i] * r[i];
+  }
+  b2 = block_sum<NT, CT>(b2, red);  // same bit pattern in every thread
+  const CT beta = sqrt(b2);
+  if (!(beta > CT(0))) return;      // r = 0: d = 0
+  for (int i = tid; i < npad; i += NT) {
+    const CT x = i < n ? r[i] / beta : CT(0);
+    v[i] = x;
+    V[i] = x;
+  }
+  if (tid == 0) g[0] = beta;
+  __syncthreads();
+  int k = 0;
+  for (int j = 0; j < mm; ++j) {
+    for (int i = tid; i < n; i += NT) {  // w = A_p v_j
+      CT s = CT(0);
+      for (int e = 0; e < K; ++e) s += to_ct(lv[(int64_t)e * npad + i]) * v[lc[(int64_t)e * npad + i]];
+      w[i] = s;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      // projections h_q = w . v_q (q <= j), reduced together
+      for (int q = 0; q <= j; ++q) {
+        const CT *__restrict__ vq = V + (int64_t)q * npad;
+        CT s = CT(0);
+        for (int i = tid; i < n; i += NT) s += w[i] * vq[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) part[wid * LDH + q] = s;
+      }
+      __syncthreads();
+      for (int q = tid; q <= j; q += NT) {
+        CT s = part[q];
+        for (int u = 1; u < NT / 32; ++u) s += part[u * LDH + q];
+        y[q] = s;
+        H[q + j * LDH] = pass == 0 ? s : H[q + j * LDH] + s;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += NT) {  // w -= sum_q h_q v_q
+        CT s = w[i];
+        for (int q = 0; q <= j; ++q) s -= y[q] * V[(int64_t)q * npad + i];
+        w[i] = s;
+      }
+      __syncthreads();  // y and part are rewritten by the next pass
+    }
+    CT h2 = CT(0);
+    for (int i = tid; i < n; i += NT) h2 += w[i] * w[i];
+    h2 = block_sum<NT, CT>(h2, red);
+    const CT hn = sqrt(h2);
+    if (tid == 0) {
+      // earlier rotations on column j, then the one that zeroes h_{j+1,j}
+      CT *hc = H + j * LDH;
+      hc[j + 1] = hn;
+      for (int q = 0; q < j; ++q) {
+        const CT a = hc[q], b = hc[q + 1];
+        hc[q] = cs[q] * a + sn[q] * b;
+        hc[q + 1] = cs[q] * b - sn[q] * a;
+      }
+      const CT a = hc[j];
+      const CT den = sqrt(a * a + hn * hn);
+      int stop = 0;
+      if (!(den > CT(0))) {
+        stop = 2;  // singular on the Krylov space: keep the j steps so far
+      } else {
+        cs[j] = a / den;
+        sn[j] = hn / den;
+        hc[j] = den;
+        hc[j + 1] = CT(0);
+        g[j + 1] = -(sn[j] * g[j]);
+        g[j] = cs[j] * g[j];
+        if (!(hn > CT(0))) stop = 1;  // exact breakdown: the space is invariant
+      }
+      flag[0] = stop;
+    }
+    __syncthreads();
+    const int stop = flag[0];
+    if (stop == 2) break;
+    k = j + 1;
+    if (stop == 1 || k == mm) break;
+    CT *__restrict__ vn = V + (int64_t)k * npad;
+    for (int i = tid; i < n; i += NT) {
+      const CT x = w[i] / hn;
+      v[i] = x;
+      vn[i] = x;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {  // R y = g, back substitution (k <= kMaxGmres)
+    for (int q = k - 1; q >= 0; --q) {
+      CT s = g[q];
+      for (int t = q + 1; t < k; ++t) s -= H[q + t * LDH] * y[t];
+      y[q] = s / H[q + q * LDH];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += NT) {  // d = V_k y
+    CT s = CT(0);
+    for (int q = 0; q < k; ++q) s += y[q] * V[(int64_t)q * npad + i];
+    d[i] = s;
+  }
+  __syncthreads();
+}
+
 // r_p = b[Omega_p] - A[Omega_p, :] x for the rows of one subdomain (thread t:
 // rows t, t + NT, ...), written to rhs in the compute type; accumulates
 // ||r||^2 over Omega_p and over its owned rows, and records for every owned
@@ -1068,7 +1317,7 @@ template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
   // band: copy rings | y | partials | window rings ; cg: r p q d ; ilu: r z p q d ;
-  // staged cg: A_p values | A_p columns | p
+  // staged cg: A_p values | A_p columns | p ; gmres: r w v d | GmresSmem
   static __host__ __device__ int band_twm(int Wmax) { return band_cols_per_warp(Wmax, NT / 32); }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
     return ((size_t)npad_max + 31) / 32 * 32;
@@ -1087,6 +1336,7 @@ struct Smem {
       const size_t vl = vec_len(npad_max);
       return (size_t)kmax * vl * 6 + vl * 4;
     }
+    if (KIND == kGMRES) return 4 * vec_len(npad_max) * sizeof(CT) + GmresSmem<CT, NT>::bytes();
     const int nv = KIND == kCG ? 4 : 5;
     return nv * vec_len(npad_max) * sizeof(CT);
   }
@@ -1121,7 +1371,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   // shared-memory carve-up
   T *ring = nullptr;
   CT *ybuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
-     *v4 = nullptr, *wbuf = nullptr;
+     *v4 = nullptr, *wbuf = nullptr, *gsm = nullptr;
   const int twm = SM::band_twm(L.Wmax);
   if (KIND == kBand) {
     ring = reinterpret_cast<T *>(smem);
@@ -1139,6 +1389,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     v2 = base + 2 * vl;
     v3 = base + 3 * vl;
     v4 = KIND == kILU ? base + 4 * vl : nullptr;
+    if (KIND == kGMRES) gsm = base + 4 * vl;
   }
   uint32_t gcount = 0;
   if (KIND == kCGS) {
@@ -1262,6 +1513,14 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
       __syncthreads();
       cg_solve<T, CT, NT>(lc, lv, K, D.n, D.npad, L.m, v0, v1, v2, v3, s_redc);
+      delta = v3;
+    } else if (KIND == kGMRES) {
+      const int32_t *lc = S.lcol + D.row_off * K;
+      const T *lv = reinterpret_cast<const T *>(S.lval) + D.row_off * K;
+      CT *V = reinterpret_cast<CT *>(S.kry) + D.row_off * S.kry_ld;
+      __syncthreads();
+      gmres_solve<T, CT, NT>(lc, lv, K, D.n, D.npad, min(L.m, S.kry_ld - 1), v0, v1, v2, v3, V, gsm,
+                             s_redc);
       delta = v3;
     } else {
       __syncthreads();
@@ -1652,6 +1911,9 @@ static int occupancy_t(size_t smem) {
     } else if (KIND_ == kCG) {                                                             \
       if (PREC_ == kF64) { if (NT_ == 512) { CALL(kCG, double, 512); } else { CALL(kCG, double, 256); } } \
       else { if (NT_ == 512) { CALL(kCG, float, 512); } else { CALL(kCG, float, 256); } }  \
+    } else if (KIND_ == kGMRES) {                                                          \
+      if (PREC_ == kF64) { if (NT_ == 512) { CALL(kGMRES, double, 512); } else { CALL(kGMRES, double, 256); } } \
+      else { if (NT_ == 512) { CALL(kGMRES, float, 512); } else { CALL(kGMRES, float, 256); } } \
     } else {                                                                               \
       if (PREC_ == kF64) { if (NT_ == 512) { CALL(kILU, double, 512); } else { CALL(kILU, double, 256); } } \
       else { if (NT_ == 512) { CALL(kILU, float, 512); } else { CALL(kILU, float, 256); } } \
@@ -1726,14 +1988,31 @@ cudaError_t launch_band_chol(const BandJob *jobs, int njobs, int max_w, double *
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_layout(int prec, const LayoutJob *jobs, int njobs, const double *band,
-                               void *fac, cudaStream_t stream) {
+cudaError_t launch_band_lu(const BandJob *jobs, int njobs, int max_w, double *band, GridCtl *ctl,
+                           cudaStream_t stream) {
+  const size_t smem = (size_t)(max_w + 1) * (2 * max_w + 1) * sizeof(double);
+  cudaError_t e = allow_max_smem((const void *)band_lu_kernel);
+  if (e != cudaSuccess) return e;
+  band_lu_kernel<<<njobs, 256, smem, stream>>>(jobs, band, ctl);
+  return cudaGetLastError();
+}
+
+template <bool LU>
+static void layout_t(int prec, const LayoutJob *jobs, int njobs, const double *band, void *fac,
+                     cudaStream_t stream) {
   if (prec == kF64)
-    band_layout_kernel<double><<<njobs, 32, 0, stream>>>(jobs, band, (double *)fac);
+    band_layout_kernel<double, LU><<<njobs, 32, 0, stream>>>(jobs, band, (double *)fac);
   else if (prec == kF32)
-    band_layout_kernel<float><<<njobs, 32, 0, stream>>>(jobs, band, (float *)fac);
+    band_layout_kernel<float, LU><<<njobs, 32, 0, stream>>>(jobs, band, (float *)fac);
   else
-    band_layout_kernel<__nv_bfloat16><<<njobs, 32, 0, stream>>>(jobs, band, (__nv_bfloat16 *)fac);
+    band_layout_kernel<__nv_bfloat16, LU><<<njobs, 32, 0, stream>>>(jobs, band,
+                                                                    (__nv_bfloat16 *)fac);
+}
+
+cudaError_t launch_band_layout(int prec, bool lu, const LayoutJob *jobs, int njobs,
+                               const double *band, void *fac, cudaStream_t stream) {
+  if (lu) layout_t<true>(prec, jobs, njobs, band, fac, stream);
+  else layout_t<false>(prec, jobs, njobs, band, fac, stream);
   return cudaGetLastError();
 }
 

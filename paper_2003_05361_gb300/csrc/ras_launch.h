@@ -8,11 +8,12 @@
 
 namespace ras {
 
-// One banded Cholesky factorisation job (one subdomain).
+// One banded factorisation job (one subdomain).
 struct BandJob {
   int32_t n;         // rows
   int32_t w;         // true half-bandwidth
-  int64_t band_off;  // offset of the row-major band (ld = w+1) in the FP64 scratch
+  int64_t band_off;  // offset of the row-major band in the FP64 scratch
+                     // (ld = w+1, lower half, for Cholesky; ld = 2w+1 for LU)
 };
 
 // One 32-row block of one subdomain for the record layout.
@@ -33,7 +34,10 @@ cudaError_t launch_copyback(const Launch &L, int nitems, cudaStream_t stream);
 cudaError_t launch_fill(double *x, double v, int64_t n, cudaStream_t stream);
 cudaError_t launch_band_chol(const BandJob *jobs, int njobs, int max_w, double *band, GridCtl *ctl,
                              cudaStream_t stream);
-cudaError_t launch_band_layout(int prec, const LayoutJob *jobs, int njobs, const double *band,
-                               void *fac, cudaStream_t stream);
+cudaError_t launch_band_lu(const BandJob *jobs, int njobs, int max_w, double *band, GridCtl *ctl,
+                           cudaStream_t stream);
+// lu: the bands hold LU factors (ld = 2w+1) instead of a Cholesky factor
+cudaError_t launch_band_layout(int prec, bool lu, const LayoutJob *jobs, int njobs,
+                               const double *band, void *fac, cudaStream_t stream);
 
 }  // namespace ras

@@ -118,7 +118,8 @@ def test_setup_rejects_invalid_matrix_before_gpu_work(defect):
     assert e.value.status == ras.RAS_EINVAL
 
 
-@pytest.mark.parametrize("what", ["part_range", "empty_part", "overlap", "kind", "bf16_cg", "iters"])
+@pytest.mark.parametrize("what", ["part_range", "empty_part", "overlap", "kind", "kind5", "bf16_cg",
+                                  "bf16_gmres", "iters", "gmres_iters0", "gmres_iters33"])
 def test_setup_rejects_invalid_options(what):
     A = problems.poisson2d(4)
     part = np.zeros(16, np.int32)
@@ -132,10 +133,28 @@ def test_setup_rejects_invalid_options(what):
         ov = -1
     elif what == "kind":
         kind = 9
+    elif what == "kind5":
+        kind = 5
     elif what == "bf16_cg":
         kind, prec = ras.RAS_LOCAL_CG, ras.RAS_BF16_STORE
+    elif what == "bf16_gmres":
+        kind, prec = ras.RAS_LOCAL_GMRES, ras.RAS_BF16_STORE
+    elif what == "gmres_iters0":
+        kind, m = ras.RAS_LOCAL_GMRES, 0
+    elif what == "gmres_iters33":
+        kind, m = ras.RAS_LOCAL_GMRES, 33  # more Arnoldi steps than the kernel keeps
     else:
         kind, m = ras.RAS_LOCAL_CG, 0
     with pytest.raises(ras.RasError) as e:
         ras.ras_setup(A, part, P, ov, kind, prec, m)
     assert e.value.status == ras.RAS_EINVAL
+
+
+@pytest.mark.parametrize("kind,N", [(ras.RAS_LOCAL_BANDLU, 120), (ras.RAS_LOCAL_BANDCHOL, 170)])
+def test_setup_rejects_too_wide_local_band_before_gpu_work(kind, N):
+    # one subdomain of an N x N grid has local half-bandwidth N: above the
+    # banded LU (112) or Cholesky (160) limit, setup stops with RAS_ENOTSUP
+    A = problems.poisson2d(N)
+    with pytest.raises(ras.RasError) as e:
+        ras.ras_setup(A, np.zeros(A.n, np.int32), 1, 0, kind, ras.RAS_FP64)
+    assert e.value.status == ras.RAS_ENOTSUP
