@@ -182,7 +182,8 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
     """Algorithmic bytes of one local update of each subdomain:
     residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p,
     local CG = nnz(A_p) (s_v + 2), once when A_p is staged in shared memory,
-    m times when it is re-read every step; band = 2 n_p (w_p + 1) s_f;
+    m times when it is re-read every step; band = 2 n_p (w_p + 1) s_f (the L
+    and L^T, or L and U, bands);
     update = 8 |O_p| written."""
     rp, ci = A.row_ptr, A.col
     rownnz = np.diff(rp)
@@ -200,7 +201,7 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
         res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
         if kind == ras.RAS_LOCAL_CG:
             loc = nnz_p * (prec_bytes + 2) * (1 if staged else m)
-        elif kind == ras.RAS_LOCAL_BANDCHOL:
+        elif kind in (ras.RAS_LOCAL_BANDCHOL, ras.RAS_LOCAL_BANDLU):
             # local half-bandwidth of A_p in ascending global order
             loc_col = np.searchsorted(om, ci[idx])
             loc_row = np.repeat(np.arange(n_p), ends - starts)
@@ -372,9 +373,13 @@ def run_ours(args):
             "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 
-    band4 = None
+    band4 = nonsym = None
     if not args.quick and world == 1:
         band4 = band_config4(dev, stream, args.band_iters)
+        try:
+            nonsym = nonsymmetric(dev, stream)
+        except Exception as e:  # reported, never fatal to the headline line
+            nonsym = {"error": f"{type(e).__name__}: {e}"}
 
     launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)
     line = {
@@ -395,6 +400,8 @@ def run_ours(args):
     }
     if band4 is not None:
         line["band_config4"] = band4
+    if nonsym is not None:
+        line["nonsymmetric"] = nonsym
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
@@ -458,6 +465,72 @@ def band_config4(dev, stream, iters: int):
                                   "algorithmic_bytes": alg,
                                   "kernel": f"ras_main_kernel<band, {name}, {launch['cta_threads']}>",
                                   "grid": launch["grid"]}}
+        ras.ras_destroy(ctx)
+    return out
+
+
+def nonsymmetric(dev, stream, reps: int = 3):
+    """Generic (nonsymmetric) systems, Sec. 4.1's LU / GMRES local solvers:
+    upwind convection-diffusion 1024^2 (bx = 0.5, by = 0.25: velocity
+    (512.5, 256.25) on the unit square, cell Peclet numbers 0.5 / 0.25), b
+    uniform seed 2, regular 16x16 = 256 subdomains, overlap 4, tol 1e-8. Time
+    to solution, sync vs async, with banded-LU local solves (factors in FP32,
+    BF16, FP64) and with 20 GMRES steps in FP32: the median of `reps` solves
+    after one untimed solve, L2 flushed (256 MB write) before each. Roofline of
+    the banded-LU FP32 synchronous kernel: algorithmic bytes (residual rows +
+    band model 2 n_p (w_p + 1) s_f + owned-row writes) per kernel time."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    n = 1024
+    A = problems.convdiff2d(n, 0.5, 0.25)
+    b = problems.rhs_uniform(A.n, 2)
+    part = ras.ras_partition_regular2d(n, n, 16, 16)
+    bd = torch.tensor(b, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peak, peak_src = measured_peaks()
+    out = {"workload": "2D upwind convection-diffusion 1024x1024 (1,048,576 unknowns, "
+                       "nonsymmetric M-matrix), bx 0.5, by 0.25, uniform RHS seed 2, regular2d "
+                       "16x16 = 256 subdomains, overlap 4, tol 1e-8, median of %d solves, L2 "
+                       "flushed before each" % reps}
+    cases = (("bandlu_fp32", ras.RAS_LOCAL_BANDLU, ras.RAS_FP32, 1, 4),
+             ("bandlu_bf16", ras.RAS_LOCAL_BANDLU, ras.RAS_BF16_STORE, 1, 2),
+             ("bandlu_fp64", ras.RAS_LOCAL_BANDLU, ras.RAS_FP64, 1, 8),
+             ("gmres20_fp32", ras.RAS_LOCAL_GMRES, ras.RAS_FP32, 20, 4))
+    for name, kind, prec, m, sb in cases:
+        ctx = ras.ras_setup(A, part, 256, 4, kind, prec, m, stream=stream)
+        row = {}
+        for mname, mode in (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)):
+            runs = []
+            for rep in range(reps + 1):
+                x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                info = ras.ras_solve(ctx, bd, x, TOL, mode)
+                if rep > 0:
+                    runs.append(info)
+            runs.sort(key=lambda i: i.solve_ms)
+            med = runs[len(runs) // 2]
+            row[mname] = {"ms": med.solve_ms, "kernel_ms": med.kernel_ms,
+                          "ms_all": [r.solve_ms for r in runs], "status": med.status,
+                          "failed": sum(1 for r in runs if r.status != 0),
+                          "iterations": med.iterations, "relres": med.relres,
+                          "updates": [med.updates_min, med.updates_median, med.updates_max]}
+            if name == "bandlu_fp32" and mode == ras.RAS_SYNC:
+                counts = ras.ras_get_update_counts(ctx)
+                per_upd = subdomain_bytes(A, ras, ctx, ras.RAS_LOCAL_BANDLU, sb, 1, True)
+                alg = float(np.dot(counts, per_upd))
+                achieved = alg / (med.kernel_ms / 1e3) / 1e9
+                launch = ras.ras_get_launch(ctx)
+                row["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak,
+                                   "unit": "GB/s", "frac": achieved / peak,
+                                   "peak_source": peak_src, "traffic": None,
+                                   "algorithmic_bytes": alg,
+                                   "kernel": f"ras_main_kernel<band (LU records), float, "
+                                             f"{launch['cta_threads']}>",
+                                   "grid": launch["grid"]}
+        out[name] = row
         ras.ras_destroy(ctx)
     return out
 
@@ -541,7 +614,9 @@ def run_profile_case(args):
                 diffusion 1024^2 (k = exp(GRF), seed 4), 16x16 = 256 subdomains
                 of 64x64, overlap 4, banded Cholesky FP32, sync (1.1 GB of
                 factor records, well over L2); its DRAM bytes per update stand
-                for the full config-4 launch."""
+                for the full config-4 launch;
+      gmres_nonsym 2D upwind convection-diffusion 1024^2 (bx 0.5, by 0.25),
+                16x16 = 256 subdomains, overlap 4, 20 GMRES steps in FP32, sync."""
     import torch
 
     import paper_2003_05361_gb300 as ras
@@ -552,6 +627,12 @@ def run_profile_case(args):
         part = ras.ras_partition_regular2d(1024, 1024, 16, 16)
         ctx = ras.ras_setup(A, part, 256, 4, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP32)
         mode, variant = ras.RAS_SYNC, "sync_band_fp32_cfg4"
+    elif args.case == "gmres_nonsym":
+        A = problems.convdiff2d(1024, 0.5, 0.25)
+        b = problems.rhs_uniform(A.n, 2)
+        part = ras.ras_partition_regular2d(1024, 1024, 16, 16)
+        ctx = ras.ras_setup(A, part, 256, 4, ras.RAS_LOCAL_GMRES, ras.RAS_FP32, 20)
+        mode, variant = ras.RAS_SYNC, "sync_gmres20_fp32_nonsym"
     elif args.case == "band_cfg1":
         A = problems.poisson2d(128)
         b, _, _ = problems.rhs_eigen2d(128)
@@ -614,7 +695,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline sample")
     ap.add_argument("--profile", action="store_true", help="run the small ncu case only")
     ap.add_argument("--profile-updates", type=int, default=20)
-    ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1", "band_cfg4s"])
+    ap.add_argument("--case", default="cg_cfg2", choices=["cg_cfg2", "band_cfg1", "band_cfg4s", "gmres_nonsym"])
     ap.add_argument("--band-iters", type=int, default=200,
                     help="sync iterations of the config-4 band roofline launch")
     ap.add_argument("--sweep", action="store_true",

@@ -1130,14 +1130,33 @@ __device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict_
       w[i] = s;
     }
     for (int pass = 0; pass < 2; ++pass) {
-      // projections h_q = w . v_q (q <= j), reduced together
-      for (int q = 0; q <= j; ++q) {
-        const CT *__restrict__ vq = V + (int64_t)q * npad;
-        CT s = CT(0);
-        for (int i = tid; i < n; i += NT) s += w[i] * vq[i];
+      // projections h_q = w . v_q (q <= j), four basis vectors per sweep over
+      // the rows (independent load streams), all reduced together
+      for (int q0 = 0; q0 <= j; q0 += 4) {
+        const int nq = min(4, j + 1 - q0);
+        const CT *__restrict__ vq = V + (int64_t)q0 * npad;
+        CT s0 = CT(0), s1 = CT(0), s2 = CT(0), s3 = CT(0);
+        for (int i = tid; i < n; i += NT) {
+          const CT wi = w[i];
+          s0 += wi * vq[i];
+          if (nq > 1) s1 += wi * vq[npad + i];
+          if (nq > 2) s2 += wi * vq[2 * (int64_t)npad + i];
+          if (nq > 3) s3 += wi * vq[3 * (int64_t)npad + i];
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) part[wid * LDH + q] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+          s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+        }
+        if (lane == 0) {
+          CT *pw = part + wid * LDH + q0;
+          pw[0] = s0;
+          if (nq > 1) pw[1] = s1;
+          if (nq > 2) pw[2] = s2;
+          if (nq > 3) pw[3] = s3;
+        }
       }
       __syncthreads();
       for (int q = tid; q <= j; q += NT) {
