@@ -1124,6 +1124,7 @@ __device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict_
   __syncthreads();
   int k = 0;
   for (int j = 0; j < mm; ++j) {
+#pragma unroll 2
     for (int i = tid; i < n; i += NT) {  // w = A_p v_j
       CT s = CT(0);
       for (int e = 0; e < K; ++e) s += to_ct(lv[(int64_t)e * npad + i]) * v[lc[(int64_t)e * npad + i]];
@@ -1131,11 +1132,13 @@ __device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict_
     }
     for (int pass = 0; pass < 2; ++pass) {
       // projections h_q = w . v_q (q <= j), four basis vectors per sweep over
-      // the rows (independent load streams), all reduced together
+      // the rows (independent load streams, rows unrolled so that the loads of
+      // several rows are in flight together), all reduced together
       for (int q0 = 0; q0 <= j; q0 += 4) {
         const int nq = min(4, j + 1 - q0);
         const CT *__restrict__ vq = V + (int64_t)q0 * npad;
         CT s0 = CT(0), s1 = CT(0), s2 = CT(0), s3 = CT(0);
+#pragma unroll 4
         for (int i = tid; i < n; i += NT) {
           const CT wi = w[i];
           s0 += wi * vq[i];
@@ -1166,6 +1169,7 @@ __device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict_
         H[q + j * LDH] = pass == 0 ? s : H[q + j * LDH] + s;
       }
       __syncthreads();
+#pragma unroll 2
       for (int i = tid; i < n; i += NT) {  // w -= sum_q h_q v_q
         CT s = w[i];
         for (int q = 0; q <= j; ++q) s -= y[q] * V[(int64_t)q * npad + i];
@@ -1223,6 +1227,7 @@ __device__ void gmres_solve(const int32_t *__restrict__ lc, const T *__restrict_
     }
   }
   __syncthreads();
+#pragma unroll 2
   for (int i = tid; i < n; i += NT) {  // d = V_k y
     CT s = CT(0);
     for (int q = 0; q < k; ++q) s += y[q] * V[(int64_t)q * npad + i];
