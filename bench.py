@@ -46,6 +46,19 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(v: float, device=None) -> float:
+    """Max of v over the ranks of the default process group (v itself when
+    there is no group or one rank): the time a step took on the slowest GPU."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def problem():
     A = problems.poisson2d(N_GRID)
     b = problems.rhs_uniform(A.n, SEED)
@@ -311,15 +324,11 @@ def run_ours(args):
                 failed.append({"ms": t, "status": info.status, "relres": info.relres,
                                "updates_median": info.updates_median})
     barrier()
-    if not times:
-        raise RuntimeError(f"no timed solve converged: {failed}")
-    med = statistics.median(times)
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([med], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        med = float(tt.item())
+    # every rank joins the reduction; a rank with no converged solve reports
+    # +inf, so all ranks see the failure together
+    med = max_over_ranks(statistics.median(times) if times else float("inf"), dev)
+    if not times or med == float("inf"):
+        raise RuntimeError(f"no timed solve converged on some rank: {failed}")
 
     # relative residual of the last result (FP64 on the device)
     relres = ras.ras_relres(ctxs[head_prec], bd, x)
@@ -351,7 +360,8 @@ def run_ours(args):
                 e2e_t.append(dt)
             else:
                 e2e_failed += 1
-        e2e = {"value": statistics.median(e2e_t) if e2e_t else None, "unit": "ms",
+        e2e_v = max_over_ranks(statistics.median(e2e_t) if e2e_t else float("inf"), dev)
+        e2e = {"value": e2e_v if e2e_v != float("inf") else None, "unit": "ms",
                "h2d_bytes_per_step": 2 * 8 * A.n, "d2h_bytes_per_step": 8 * A.n,
                "failed_steps": e2e_failed}
 
