@@ -83,9 +83,9 @@ def _load():
     lib.or_pcg_ilu0.restype = None
     lib.or_residual.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, _F64P, C.c_void_p]
     lib.or_residual.restype = C.c_double
-    lib.or_ras_sync.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, _I32P, C.c_int, C.c_int,
-                                C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, _F64P,
-                                C.c_void_p, C.POINTER(C.c_int32)]
+    lib.or_ras_sync_ex.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, _I32P, C.c_int, C.c_int,
+                                   C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                   C.c_int, _F64P, C.c_void_p, C.POINTER(C.c_int32)]
     _lib = lib
     return lib
 
@@ -230,15 +230,17 @@ def residual(A, b: np.ndarray, x: np.ndarray):
 
 def ras_sync(A, b, part, P: int, gamma: int, kind: int = BANDCHOL, prec: int = FP64,
              m: int = 20, tol: float = 1e-8, max_iter: int = 100000, nthreads: int = 1,
-             x0=None, allow_noconv: bool = False):
-    """Synchronous RAS. Returns (x, iterations, relres_history)."""
+             x0=None, allow_noconv: bool = False, oras_alpha: float = 0.0):
+    """Synchronous RAS (optimized local matrices when oras_alpha != 0).
+    Returns (x, iterations, relres_history)."""
     rp, ci, val = _csr(A)
     x = np.zeros(A.n) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
     hist = np.zeros(max_iter + 1)
     it = C.c_int32(0)
-    rc = _load().or_ras_sync(A.n, rp, ci, val, np.ascontiguousarray(b, dtype=np.float64),
-                             np.ascontiguousarray(part, dtype=np.int32), P, gamma, kind, prec, m,
-                             tol, max_iter, nthreads, x, hist.ctypes.data, C.byref(it))
+    rc = _load().or_ras_sync_ex(A.n, rp, ci, val, np.ascontiguousarray(b, dtype=np.float64),
+                                np.ascontiguousarray(part, dtype=np.int32), P, gamma, kind, prec,
+                                m, oras_alpha, tol, max_iter, nthreads, x, hist.ctypes.data,
+                                C.byref(it))
     if rc and not (rc == ENOCONV and allow_noconv):
         raise OracleError(f"ras_sync: {rc}")
     k = it.value

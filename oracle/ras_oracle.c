@@ -726,8 +726,8 @@ static void or_sub_free(or_sub *s) {
 /* Set up subdomain p: overlap maps, local matrix A_p (Sec. 3.2.2) and its
  * factorisation (done once, Sec. 3.3.1). */
 static int or_sub_setup(int n, const int32_t *rp, const int32_t *ci, const double *val,
-                        const int32_t *part, int P, int p, int gamma, int kind, int32_t *g2l,
-                        or_sub *s) {
+                        const int32_t *part, int P, int p, int gamma, int kind, double alpha,
+                        int32_t *g2l, or_sub *s) {
   memset(s, 0, sizeof(*s));
   int32_t *omega = (int32_t *)malloc(sizeof(int32_t) * n);
   uint8_t *owned = (uint8_t *)malloc(n);
@@ -764,6 +764,19 @@ static int or_sub_setup(int n, const int32_t *rp, const int32_t *ci, const doubl
       if (dd > w) w = dd;
     }
     s->lrp[t + 1] = (int32_t)c;
+  }
+  if (alpha != 0.0) {
+    /* optimized (Robin-type) interface condition: every exterior neighbour
+     * value u_j of row t is replaced by alpha * u_t, i.e. the exterior
+     * couplings of the row, times alpha, join its diagonal */
+    for (int t = 0; t < no; ++t) {
+      int g = omega[t];
+      double ext = 0.0;
+      for (int k = rp[g]; k < rp[g + 1]; ++k)
+        if (g2l[ci[k]] < 0) ext += val[k];
+      for (int k = s->lrp[t]; k < s->lrp[t + 1]; ++k)
+        if (s->lci[k] == t) s->lval[k] += alpha * ext;
+    }
   }
   for (int t = 0; t < no; ++t) g2l[omega[t]] = -1;
   s->w = w;
@@ -813,7 +826,15 @@ static void or_sub_solve(const or_sub *s, int kind, int prec, int m, double *rhs
 int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *b,
                 const int32_t *part, int P, int gamma, int kind, int prec, int m, double tol,
                 int max_iter, int nthreads, double *x, double *hist, int32_t *iters) {
-  if (n <= 0 || P <= 0 || gamma < 0 || max_iter < 0) return OR_EINVAL;
+  return or_ras_sync_ex(n, rp, ci, val, b, part, P, gamma, kind, prec, m, 0.0, tol, max_iter,
+                        nthreads, x, hist, iters);
+}
+
+int or_ras_sync_ex(int n, const int32_t *rp, const int32_t *ci, const double *val,
+                   const double *b, const int32_t *part, int P, int gamma, int kind, int prec,
+                   int m, double alpha, double tol, int max_iter, int nthreads, double *x,
+                   double *hist, int32_t *iters) {
+  if (n <= 0 || P <= 0 || gamma < 0 || max_iter < 0 || !isfinite(alpha)) return OR_EINVAL;
   if (kind < OR_BANDCHOL || kind > OR_GMRES || prec < OR_FP64 || prec > OR_BF16) return OR_EINVAL;
   if (prec == OR_BF16 && kind != OR_BANDCHOL && kind != OR_BANDLU) return OR_EINVAL;
   for (int i = 0; i < n; ++i)
@@ -823,7 +844,7 @@ int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, 
   for (int i = 0; i < n; ++i) g2l[i] = -1;
   int rc = OR_OK;
   for (int p = 0; p < P && rc == OR_OK; ++p)
-    rc = or_sub_setup(n, rp, ci, val, part, P, p, gamma, kind, g2l, &subs[p]);
+    rc = or_sub_setup(n, rp, ci, val, part, P, p, gamma, kind, alpha, g2l, &subs[p]);
   free(g2l);
   double *r = (double *)malloc(sizeof(double) * n);
   double *xn = (double *)malloc(sizeof(double) * n);

@@ -93,5 +93,19 @@ double or_residual(int n, const int32_t *rp, const int32_t *ci, const double *va
 int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *b,
                 const int32_t *part, int P, int gamma, int kind, int prec, int m, double tol,
                 int max_iter, int nthreads, double *x, double *hist, int32_t *iters);
+/*
+ * Same with optimized (Robin-type) local matrices, the Optimized RAS the
+ * paper names as future work (Sec. 6): in each local matrix A_p every value
+ * of an exterior neighbour j in E_p is replaced by alpha times the value of
+ * the row's own unknown, i.e. A_p[t][t] += alpha * sum_{j in E_p} A[i][j]
+ * (i the global row of t). alpha = 0 is RAS (Dirichlet data at E_p); on the
+ * 5-point Laplacian alpha is the ghost-value ratio of a Robin condition
+ * du/dn + p u = 0 at the midpoint of the cut edge, p = (2/h)(1-alpha)/(1+alpha).
+ * The residual stays that of A, so the fixed point is unchanged.
+ */
+int or_ras_sync_ex(int n, const int32_t *rp, const int32_t *ci, const double *val,
+                   const double *b, const int32_t *part, int P, int gamma, int kind, int prec,
+                   int m, double alpha, double tol, int max_iter, int nthreads, double *x,
+                   double *hist, int32_t *iters);
 
 #endif

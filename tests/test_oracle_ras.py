@@ -325,3 +325,93 @@ def test_convdiff_eigenvector_rhs_error_bound():
     kappa = np.linalg.cond(dense(A))
     assert np.linalg.norm(x - u) / np.linalg.norm(u) <= kappa * hist[-1]
     assert np.linalg.norm(x - u) / np.linalg.norm(u) <= 1e-7
+
+
+# ---------------------------------------------------------------- optimized local matrices (ORAS)
+
+def oras_operators(S, part, P, gamma, A, alpha):
+    """Explicit operators with optimized local matrices, built from the dense
+    matrix: A~_p = S[om, om] + alpha * diag(S[om, outside] row sums)."""
+    n = S.shape[0]
+    M = np.zeros((n, n))
+    G = np.zeros((n, n), bool)
+    for i in range(n):
+        G[i, A.col[A.row_ptr[i]:A.row_ptr[i + 1]]] = True
+    for p in range(P):
+        inside = part == p
+        for _ in range(gamma):
+            inside = inside | G[inside].any(0)
+        om = np.nonzero(inside)[0]
+        Ap = S[np.ix_(om, om)] + alpha * np.diag(S[np.ix_(om, np.nonzero(~inside)[0])].sum(1))
+        R = np.zeros((om.size, n))
+        R[np.arange(om.size), om] = 1.0
+        Rt = R.copy()
+        Rt[part[om] != p] = 0.0
+        M += Rt.T @ np.linalg.solve(Ap, R)
+    return np.eye(n) - M @ S, M
+
+
+def test_oras_alpha_zero_is_ras_bitwise():
+    A = problems.poisson2d(24)
+    b = problems.rhs_uniform(A.n, 7)
+    part = oracle.partition_regular2d(24, 24, 2, 3)
+    x0, h0 = iterate(A, b, part, 6, 2, 9)
+    x1, h1 = iterate(A, b, part, 6, 2, 9, oras_alpha=0.0)
+    assert np.array_equal(x0, x1) and np.array_equal(h0, h1)
+
+
+@pytest.mark.parametrize("case,kind,alpha", [("poisson", oracle.BANDCHOL, 0.6),
+                                             ("poisson", oracle.BANDCHOL, -0.4),
+                                             ("convdiff", oracle.BANDLU, 0.5),
+                                             ("diffusion", oracle.BANDCHOL, 0.7)])
+def test_oras_iteration_matrix(case, kind, alpha):
+    N = 8
+    if case == "poisson":
+        A = problems.poisson2d(N)
+    elif case == "convdiff":
+        A = problems.convdiff2d(N, 1.0, -0.5)
+    else:
+        A = problems.diffusion2d(N, problems.grf_coefficient(N, 5))
+    S = dense(A)
+    b = problems.rhs_uniform(A.n, 3)
+    part = oracle.partition_regular2d(N, N, 2, 2)
+    T, M = oras_operators(S, part, 4, 1, A, alpha)
+    xk = np.zeros(A.n)
+    for k in range(1, 6):
+        xk = T @ xk + M @ b
+        x, _ = iterate(A, b, part, 4, 1, k, kind=kind, oras_alpha=alpha)
+        assert np.linalg.norm(x - xk) <= 1e-12 * np.linalg.norm(xk)
+
+
+def test_oras_fixed_point_and_robin_speedup():
+    # the residual stays that of A, so the limit is A^-1 b; a Robin-type
+    # condition (alpha toward 1: p = (2/h)(1-alpha)/(1+alpha) on the Laplacian)
+    # cuts the iteration count at overlap 2 and 4
+    N = 64
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 1)
+    part = oracle.partition_regular2d(N, N, 4, 4)
+    xs = spla.spsolve(A.to_scipy().tocsc(), b)
+    for gamma in (2, 4):
+        its = []
+        for alpha in (0.0, 0.5, 0.8):
+            x, it, hist = oracle.ras_sync(A, b, part, 16, gamma, tol=1e-9, oras_alpha=alpha)
+            assert hist[-1] < 1e-9
+            assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-7
+            its.append(it)
+        assert its[0] > its[1] > its[2]
+        assert its[2] < 0.6 * its[0]
+
+
+def test_oras_cg_with_many_steps_equals_band():
+    N = 14
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 9)
+    part = oracle.partition_regular2d(N, N, 2, 2)
+    xd, _ = iterate(A, b, part, 4, 1, 6, oras_alpha=0.5)
+    xc, _ = iterate(A, b, part, 4, 1, 6, kind=oracle.CG, m=200, oras_alpha=0.5)
+    xi, _ = iterate(A, b, part, 4, 1, 6, kind=oracle.GMRES, m=200, oras_alpha=0.5)
+    assert np.linalg.norm(xd - xc) <= 1e-10 * np.linalg.norm(xd)
+    assert np.linalg.norm(xd - xi) <= 1e-10 * np.linalg.norm(xd)
+    with pytest.raises(oracle.OracleError):
+        oracle.ras_sync(A, b, part, 4, 1, oras_alpha=float("nan"))
