@@ -383,13 +383,17 @@ def run_ours(args):
             "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 
-    band4 = nonsym = None
+    band4 = nonsym = oras = None
     if not args.quick and world == 1:
         band4 = band_config4(dev, stream, args.band_iters)
         try:
             nonsym = nonsymmetric(dev, stream)
         except Exception as e:  # reported, never fatal to the headline line
             nonsym = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            oras = oras_section(dev, stream)
+        except Exception as e:
+            oras = {"error": f"{type(e).__name__}: {e}"}
 
     launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)
     line = {
@@ -412,6 +416,8 @@ def run_ours(args):
         line["band_config4"] = band4
     if nonsym is not None:
         line["nonsymmetric"] = nonsym
+    if oras is not None:
+        line["oras"] = oras
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
@@ -541,6 +547,42 @@ def nonsymmetric(dev, stream, reps: int = 3):
                                              f"{launch['cta_threads']}>",
                                    "grid": launch["grid"]}
         out[name] = row
+        ras.ras_destroy(ctx)
+    return out
+
+
+def oras_section(dev, stream, max_updates: int = 12000):
+    """Optimized RAS (the paper's future work, Sec. 6) on the benchmark problem
+    (2D Poisson 1024^2, b seed 1, regular 16x16 = 256 subdomains, overlap 4)
+    with banded-Cholesky local solves in FP32: time to 1e-8 for interface
+    parameters alpha = 0 (RAS), 0.5, 0.8, 0.9, sync and async, one timed solve
+    after an untimed one, L2 flushed before each; every solve capped at
+    `max_updates` updates per subdomain (a diverging alpha ends RAS_ENOCONV)."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    A, b = problem()
+    part = ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX)
+    bd = torch.tensor(b, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    out = {"workload": "2D Poisson 5-point 1024x1024 (1,048,576 unknowns), uniform RHS seed 1, "
+                       "regular2d 16x16 = 256 subdomains, overlap 4, banded Cholesky FP32 local "
+                       "solves on optimized local matrices A_p + alpha diag(exterior couplings), "
+                       "tol 1e-8, one timed solve per point, L2 flushed before each",
+           "points": []}
+    for alpha in (0.0, 0.5, 0.8, 0.9):
+        ctx = ras.ras_setup(A, part, PX * PX, GAMMA, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP32,
+                            stream=stream, oras_alpha=alpha)
+        for mname, mode in (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)):
+            for rep in range(2):
+                x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                info = ras.ras_solve(ctx, bd, x, TOL, mode, max_updates)
+            out["points"].append({"alpha": alpha, "mode": mname, "ms": info.solve_ms,
+                                  "status": info.status, "iterations": info.iterations,
+                                  "relres": info.relres})
         ras.ras_destroy(ctx)
     return out
 

@@ -102,6 +102,17 @@ typedef struct {
   int32_t prec;        /* ras_prec */
   int32_t inner_iters; /* CG / PCG / GMRES steps per local solve (ignored by the
                           banded solvers) */
+  int32_t reserved_;   /* set to 0 */
+  double oras_alpha;   /* Optimized RAS (named as future work in Sec. 6): every
+                          local matrix A_p takes, on each row, the row's couplings
+                          to points outside Omega_p times oras_alpha onto its
+                          diagonal, i.e. an exterior neighbour's value is replaced
+                          by oras_alpha times the row's own (a Robin-type interface
+                          condition; on the 5-point Laplacian the Robin parameter
+                          p = (2/h)(1 - a)/(1 + a)). 0 = RAS. The outer residual
+                          keeps A, so the solution is unchanged; a too large value
+                          can make the iteration diverge (RAS_ENOCONV) or a local
+                          factorisation fail (RAS_ENOTSPD). Must be finite. */
 } ras_local_solver;
 
 /* Result of one solve. */

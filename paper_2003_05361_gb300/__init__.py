@@ -35,7 +35,8 @@ class ras_csr(C.Structure):
 
 
 class ras_local_solver(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("prec", C.c_int32), ("inner_iters", C.c_int32)]
+    _fields_ = [("kind", C.c_int32), ("prec", C.c_int32), ("inner_iters", C.c_int32),
+                ("reserved_", C.c_int32), ("oras_alpha", C.c_double)]
 
 
 class ras_solve_info(C.Structure):
@@ -185,12 +186,13 @@ class RasContext:
 
 
 def ras_setup(A, partition, num_parts: int, overlap: int, kind: int = RAS_LOCAL_BANDCHOL,
-              prec: int = RAS_FP64, inner_iters: int = 20, stream=None) -> RasContext:
+              prec: int = RAS_FP64, inner_iters: int = 20, stream=None,
+              oras_alpha: float = 0.0) -> RasContext:
     h = _HostCSR(A)
     part = np.ascontiguousarray(partition, dtype=np.int32)
     if part.size != h.s.n:
         raise ValueError("partition must have one entry per row")
-    ls = ras_local_solver(kind, prec, inner_iters)
+    ls = ras_local_solver(kind, prec, inner_iters, 0, oras_alpha)
     out = C.c_void_p()
     _check(load().ras_setup(C.byref(h.s), part.ctypes.data, num_parts, overlap, C.byref(ls),
                             _stream_handle(stream), C.byref(out)), "ras_setup")

@@ -685,6 +685,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   if (lsv->prec == RAS_BF16_STORE && !banded) return RAS_EINVAL;
   if (!banded && lsv->inner_iters <= 0) return RAS_EINVAL;
   if (lsv->kind == RAS_LOCAL_GMRES && lsv->inner_iters > kMaxGmres) return RAS_EINVAL;
+  if (!std::isfinite(lsv->oras_alpha)) return RAS_EINVAL;
   ras_status st = check_csr(A);
   if (st != RAS_OK) return st;
   const int n = A->n;
@@ -772,6 +773,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   std::vector<double> band;  // FP64 bands for the GPU factorisation
   std::vector<int64_t> band_off(P, 0);
   const bool lu = kind == RAS_LOCAL_BANDLU;
+  const double alpha = lsv->oras_alpha;
   if (!banded) {
     lcol.assign(rows * K, 0);
     lval64.assign(rows * K, 0.0);
@@ -801,13 +803,22 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       gidx[ro + i] = g;
       ownf[ro + i] = mp.owned[i];
       if (mp.owned[i]) own[d.own_off + t_own++] = i;
-      int k = 0, kl = 0;
+      int k = 0, kl = 0, diag_kl = -1;
+      int64_t diag_lva = -1;
+      double ext = 0.0;  // couplings of row i to points outside Omega_p
       for (int e = A->row_ptr[g]; e < A->row_ptr[g + 1]; ++e, ++k) {
         const int col = A->col_idx[e];
         rcol[ro * K + (int64_t)k * d.npad + i] = col;
         rval[ro * K + (int64_t)k * d.npad + i] = A->val[e];
         const int j = local_index(mp.omega, col);
-        if (j < 0) continue;
+        if (j < 0) {
+          ext += A->val[e];
+          continue;
+        }
+        if (j == i) {
+          diag_kl = kl;
+          diag_lva = (int64_t)lva.size();
+        }
         if (lu) {
           band[band_off[p] + (int64_t)i * (2 * mp.w + 1) + (j - i + mp.w)] = A->val[e];
         } else if (banded) {
@@ -820,6 +831,17 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
             lva.push_back(A->val[e]);
           }
           ++kl;
+        }
+      }
+      if (alpha != 0.0 && ext != 0.0) {
+        // Optimized RAS: exterior neighbour values replaced by alpha times the
+        // row's own value, so alpha * ext joins the local diagonal (the
+        // residual operator rval keeps A)
+        if (lu) band[band_off[p] + (int64_t)i * (2 * mp.w + 1) + mp.w] += alpha * ext;
+        else if (banded) band[band_off[p] + (int64_t)i * (mp.w + 1) + mp.w] += alpha * ext;
+        else {
+          lval64[ro * K + (int64_t)diag_kl * d.npad + i] += alpha * ext;
+          if (kind == RAS_LOCAL_ILU0_CG) lva[diag_lva] += alpha * ext;
         }
       }
       for (; k < K; ++k) rcol[ro * K + (int64_t)k * d.npad + i] = g;  // zero-valued padding

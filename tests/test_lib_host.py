@@ -119,11 +119,12 @@ def test_setup_rejects_invalid_matrix_before_gpu_work(defect):
 
 
 @pytest.mark.parametrize("what", ["part_range", "empty_part", "overlap", "kind", "kind5", "bf16_cg",
-                                  "bf16_gmres", "iters", "gmres_iters0", "gmres_iters33"])
+                                  "bf16_gmres", "iters", "gmres_iters0", "gmres_iters33",
+                                  "oras_nan", "oras_inf"])
 def test_setup_rejects_invalid_options(what):
     A = problems.poisson2d(4)
     part = np.zeros(16, np.int32)
-    P, ov, kind, prec, m = 1, 1, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP64, 20
+    P, ov, kind, prec, m, alpha = 1, 1, ras.RAS_LOCAL_BANDCHOL, ras.RAS_FP64, 20, 0.0
     if what == "part_range":
         part[3] = 2
         P = 2
@@ -143,10 +144,14 @@ def test_setup_rejects_invalid_options(what):
         kind, m = ras.RAS_LOCAL_GMRES, 0
     elif what == "gmres_iters33":
         kind, m = ras.RAS_LOCAL_GMRES, 33  # more Arnoldi steps than the kernel keeps
+    elif what == "oras_nan":
+        alpha = float("nan")
+    elif what == "oras_inf":
+        alpha = float("inf")
     else:
         kind, m = ras.RAS_LOCAL_CG, 0
     with pytest.raises(ras.RasError) as e:
-        ras.ras_setup(A, part, P, ov, kind, prec, m)
+        ras.ras_setup(A, part, P, ov, kind, prec, m, oras_alpha=alpha)
     assert e.value.status == ras.RAS_EINVAL
 
 
