@@ -163,3 +163,36 @@ def test_setup_rejects_too_wide_local_band_before_gpu_work(kind, N):
     with pytest.raises(ras.RasError) as e:
         ras.ras_setup(A, np.zeros(A.n, np.int32), 1, 0, kind, ras.RAS_FP64)
     assert e.value.status == ras.RAS_ENOTSUP
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    # the ctypes mirrors must have the C layout: compile a probe against
+    # include/ras.h (host compiler only) and compare sizes and field offsets
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [ras.ras_csr, ras.ras_local_solver, ras.ras_solve_info, ras.ras_tune_result]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ras.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.split("\n") if l)
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == C.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, f"{name}.{f}"
