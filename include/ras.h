@@ -260,10 +260,11 @@ ras_status ras_get_info(const ras_ctx *ctx, int32_t *num_parts, int32_t *n, int3
 /* Per-subdomain local-update counts of the last solve: counts[num_parts]. */
 ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
 
-/* Launch shape the context uses: kernel_variant 0 banded Cholesky, 1 CG
- * reading A_p from global memory, 2 ILU(0)-PCG, 3 CG with A_p staged in
- * shared memory; threads per CTA; CTAs (one cooperative launch); CG / PCG
- * steps per local solve. Any pointer may be NULL. */
+/* Launch shape the context uses: kernel_variant 0 banded triangular solves
+ * (Cholesky or LU factors), 1 CG reading A_p from global memory, 2
+ * ILU(0)-PCG, 3 CG with A_p staged in shared memory, 4 GMRES; threads per
+ * CTA; CTAs (one cooperative launch); CG / PCG / GMRES steps per local solve.
+ * Any pointer may be NULL. */
 ras_status ras_get_launch(const ras_ctx *ctx, int32_t *kernel_variant, int32_t *cta_threads,
                           int32_t *grid, int32_t *inner_iters);
 
