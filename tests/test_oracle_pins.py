@@ -464,6 +464,83 @@ def test_gmres_exact_breakdown_and_zero_rhs():
     assert np.array_equal(oracle.gmres(D, np.zeros(n), 5), np.zeros(n))
 
 
+def _gmres_float32(A, r, m):
+    """GMRES in numpy float32 scalars, one operation at a time in the oracle's
+    order (MGS, Givens, back substitution): every float32 operation is
+    correctly rounded, so this is plain FP32 arithmetic."""
+    f = np.float32
+    n = A.n
+    val = A.val.astype(f)
+    rr = r.astype(f)
+    b2 = f(0)
+    for i in range(n):
+        b2 = f(b2 + f(rr[i] * rr[i]))
+    beta = f(np.sqrt(b2))
+    m = min(m, n)
+    V = [np.array([f(rr[i] / beta) for i in range(n)], dtype=f)]
+    H = np.zeros((m + 1, m), dtype=f)
+    cs, sn, g = np.zeros(m, f), np.zeros(m, f), np.zeros(m + 1, f)
+    g[0] = beta
+    k = 0
+    for j in range(m):
+        vj = V[j]
+        w = np.zeros(n, f)
+        for i in range(n):
+            s = f(0)
+            for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                s = f(s + f(val[e] * vj[A.col[e]]))
+            w[i] = s
+        for q in range(j + 1):
+            h = f(0)
+            for i in range(n):
+                h = f(h + f(w[i] * V[q][i]))
+            H[q, j] = h
+            for i in range(n):
+                w[i] = f(w[i] - f(h * V[q][i]))
+        hn2 = f(0)
+        for i in range(n):
+            hn2 = f(hn2 + f(w[i] * w[i]))
+        hn = f(np.sqrt(hn2))
+        H[j + 1, j] = hn
+        for q in range(j):
+            a, b = H[q, j], H[q + 1, j]
+            H[q, j] = f(f(cs[q] * a) + f(sn[q] * b))
+            H[q + 1, j] = f(f(cs[q] * b) - f(sn[q] * a))
+        a = H[j, j]
+        den = f(np.sqrt(f(f(a * a) + f(hn * hn))))
+        cs[j], sn[j] = f(a / den), f(hn / den)
+        H[j, j], H[j + 1, j] = den, f(0)
+        g[j + 1] = -f(sn[j] * g[j])
+        g[j] = f(cs[j] * g[j])
+        k = j + 1
+        if hn == 0:
+            break
+        V.append(np.array([f(w[i] / hn) for i in range(n)], dtype=f))
+    y = np.zeros(k, f)
+    for q in range(k - 1, -1, -1):
+        s = g[q]
+        for t in range(q + 1, k):
+            s = f(s - f(H[q, t] * y[t]))
+        y[q] = f(s / H[q, q])
+    d = np.zeros(n, f)
+    for i in range(n):
+        s = f(0)
+        for q in range(k):
+            s = f(s + f(y[q] * V[q][i]))
+        d[i] = s
+    return d.astype(np.float64)
+
+
+def test_gmres_fp32_mode_is_float32_arithmetic():
+    # the oracle computes in double and rounds each result to float; for
+    # + - * / and sqrt of floats that is the correctly rounded float result,
+    # so it must equal plain float32 arithmetic bit for bit
+    A = problems.convdiff2d(5, 0.9, -0.4)
+    r = problems.rhs_uniform(A.n, 13)
+    for m in (1, 3, 7):
+        assert np.array_equal(oracle.gmres(A, r, m, oracle.FP32), _gmres_float32(A, r, m)), m
+
+
 def test_gmres_fp32_within_rounding():
     A = problems.convdiff2d(16, 0.5, 0.5)
     r = problems.rhs_uniform(A.n, 11)
