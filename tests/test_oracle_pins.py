@@ -392,6 +392,22 @@ def test_band_lu_solve_low_precision_error_bound(prec, eps):
     err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
     assert err <= 4 * kappa * (N + 1) * eps
     assert err >= 1e-2 * eps  # really computed in reduced precision
+    if prec == oracle.FP32:
+        # float32 substitutions with the factors rounded to float32
+        Ff = F.astype(np.float32)
+        y = rhs.astype(np.float32)
+        n, w = A.n, N
+        for i in range(n):
+            acc = y[i]
+            for k in range(max(0, i - w), i):
+                acc = np.float32(acc - np.float32(Ff[i, k - i + w] * y[k]))
+            y[i] = acc
+        for i in range(n - 1, -1, -1):
+            acc = y[i]
+            for k in range(i + 1, min(n - 1, i + w) + 1):
+                acc = np.float32(acc - np.float32(Ff[i, k - i + w] * y[k]))
+            y[i] = np.float32(acc / Ff[i, w])
+        assert np.array_equal(x, y.astype(np.float64))
 
 
 # ---------------------------------------------------------------- GMRES
