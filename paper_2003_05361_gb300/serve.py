@@ -23,8 +23,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (RAS_ASYNC, RAS_FP32, RAS_LOCAL_BANDCHOL, ras_batch_step, ras_destroy,
-               ras_get_info, ras_partition_regular2d, ras_setup, ras_solve_begin)
+from . import (RAS_ASYNC, RAS_ENOTSUP, RAS_FP32, RAS_LOCAL_BANDCHOL, ras_batch_step,
+               ras_destroy, ras_get_info, ras_partition_regular2d, ras_setup, ras_solve_begin)
 
 
 @dataclass
@@ -48,6 +48,7 @@ class Record:
     iterations: int
     relres: float
     device_bytes: int
+    rejected: bool = False  # could never fit the slots or the budget (status RAS_ENOTSUP)
 
     @property
     def latency(self) -> float:
@@ -87,7 +88,9 @@ class Server:
     """Serving configuration. step_limit: local updates per subdomain (async)
     or iterations (sync) per batched launch; max_parts: subdomain slots shared
     by the active systems; budget_bytes: HBM budget for active contexts
-    (default 0.8 x free device memory)."""
+    (default 0.8 x free device memory). A request that needs more slots or
+    bytes than these limits allow even alone is rejected on arrival (record
+    status RAS_ENOTSUP), never queued."""
 
     mode: int = RAS_ASYNC
     prec: int = RAS_FP32
@@ -124,15 +127,32 @@ class Server:
         nbytes = ras_get_info(ctx)["device_bytes"] + 3 * 8 * A.n
         return _Active(req, ctx, bd, x, A.n, px * px, nbytes, 0.0, time.perf_counter() - t0)
 
-    def run(self, requests, stream=None):
-        """Serves `requests` (sorted by arrival) in real time; returns summary stats."""
+    # device-facing steps of the loop (the scheduler below only calls these)
+    def _default_stream(self):
         import torch
 
+        return torch.cuda.current_stream()
+
+    def _free_device_bytes(self) -> int:
+        import torch
+
+        return torch.cuda.mem_get_info()[0]
+
+    def _step(self, ctxs):
+        return ras_batch_step(ctxs, self.mode, self.step_limit)
+
+    def _release(self, a: _Active) -> None:
+        ras_destroy(a.ctx)
+
+    def _solution(self, a: _Active):
+        return a.x.cpu().numpy()
+
+    def run(self, requests, stream=None):
+        """Serves `requests` (sorted by arrival) in real time; returns summary stats."""
         if stream is None:
-            stream = torch.cuda.current_stream()
+            stream = self._default_stream()
         if self.budget_bytes <= 0:
-            free, _ = torch.cuda.mem_get_info()
-            self.budget_bytes = int(0.8 * free)
+            self.budget_bytes = int(0.8 * self._free_device_bytes())
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         inflight = deque()  # futures of setups in progress
         active: list[_Active] = []
@@ -149,6 +169,14 @@ class Server:
                     r = pending[0]
                     px = math.ceil(r.side / self.block)
                     est = self._estimate(r.side)
+                    if px * px > self.max_parts or est > self.budget_bytes:
+                        # can never fit, even alone: reject it rather than
+                        # block the queue behind it
+                        pending.popleft()
+                        self.records.append(Record(r.rid, r.side, r.side * r.side, r.arrival,
+                                                   now, now, now, RAS_ENOTSUP, 0, float("nan"),
+                                                   est, rejected=True))
+                        continue
                     if used_parts + px * px > self.max_parts or used_bytes + est > self.budget_bytes:
                         break
                     pending.popleft()
@@ -171,7 +199,7 @@ class Server:
                     elif pending:
                         time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                     continue
-                done, infos = ras_batch_step([a.ctx for a in active], self.mode, self.step_limit)
+                done, infos = self._step([a.ctx for a in active])
                 steps += 1
                 tnow = time.perf_counter() - t0
                 keep = []
@@ -183,8 +211,8 @@ class Server:
                                                a.admitted, a.started, tnow, info.status,
                                                info.iterations, info.relres, a.nbytes))
                     if self.keep_solutions:
-                        self.solutions[a.req.rid] = a.x.cpu().numpy()
-                    ras_destroy(a.ctx)
+                        self.solutions[a.req.rid] = self._solution(a)
+                    self._release(a)
                     used_bytes -= a.nbytes
                     used_parts -= a.parts
                 active = keep
@@ -194,28 +222,31 @@ class Server:
         return self.summary(wall, steps)
 
     def summary(self, wall: float, steps: int) -> dict:
-        lat = sorted(r.latency for r in self.records)
+        rejected = sum(1 for r in self.records if r.rejected)
+        served = [r for r in self.records if not r.rejected]
+        lat = sorted(r.latency for r in served)
         if not lat:
-            return {"completed": 0}
+            return {"completed": 0, "rejected": rejected}
 
         def pct(q):
             return lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
 
-        first = min(r.arrival for r in self.records)
-        last = max(r.finished for r in self.records)
-        wait = [r.admitted - r.arrival for r in self.records]
-        setup = [r.started - r.admitted for r in self.records]
-        run = [r.finished - r.started for r in self.records]
+        first = min(r.arrival for r in served)
+        last = max(r.finished for r in served)
+        wait = [r.admitted - r.arrival for r in served]
+        setup = [r.started - r.admitted for r in served]
+        run = [r.finished - r.started for r in served]
         return {
             "completed": len(lat),
-            "failed": sum(1 for r in self.records if r.status != 0),
+            "rejected": rejected,
+            "failed": sum(1 for r in served if r.status != 0),
             "p50_ms": 1e3 * pct(0.50),
             "p99_ms": 1e3 * pct(0.99),
             "mean_ms": 1e3 * statistics.fmean(lat),
             "solves_per_s": len(lat) / max(last - first, 1e-9),
             "wall_s": wall,
             "steps": steps,
-            "max_relres": max(r.relres for r in self.records),
+            "max_relres": max(r.relres for r in served),
             # where a request's latency goes: waiting for admission, host and
             # device setup (maps, factorisation), and solving in the batch
             "admission_wait_ms_mean": 1e3 * statistics.fmean(wait),
