@@ -86,6 +86,12 @@ def _load():
     lib.or_ras_sync_ex.argtypes = [C.c_int, _I32P, _I32P, _F64P, _F64P, _I32P, C.c_int, C.c_int,
                                    C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                    C.c_int, _F64P, C.c_void_p, C.POINTER(C.c_int32)]
+    lib.or_ras_new.argtypes = [C.c_int, _I32P, _I32P, _F64P, _I32P, C.c_int, C.c_int, C.c_int,
+                               C.c_int, C.c_int, C.c_double, C.POINTER(C.c_void_p)]
+    lib.or_ras_iterate.argtypes = [C.c_void_p, _F64P, C.c_double, C.c_int, C.c_int, _F64P,
+                                   C.c_void_p, C.POINTER(C.c_int32)]
+    lib.or_ras_free.argtypes = [C.c_void_p]
+    lib.or_ras_free.restype = None
     _lib = lib
     return lib
 
@@ -245,3 +251,58 @@ def ras_sync(A, b, part, P: int, gamma: int, kind: int = BANDCHOL, prec: int = F
         raise OracleError(f"ras_sync: {rc}")
     k = it.value
     return x, k, hist[: k + 1].copy()
+
+
+class RasSetup:
+    """Synchronous RAS split as Algorithm 1 splits it: the constructor does the
+    set-up (overlap maps, local matrices, factorisations; untimed in Sec. 3.1),
+    iterate() runs RAS iterations from x with the same arithmetic as
+    ras_sync(). setup_s is the wall time of the set-up."""
+
+    def __init__(self, A, part, P: int, gamma: int, kind: int = BANDCHOL, prec: int = FP64,
+                 m: int = 20, oras_alpha: float = 0.0):
+        import time
+
+        self._arrays = _csr(A)  # the C handle points into these
+        self._part = np.ascontiguousarray(part, dtype=np.int32)
+        self.n = A.n
+        h = C.c_void_p()
+        t0 = time.perf_counter()
+        rp, ci, val = self._arrays
+        rc = _load().or_ras_new(A.n, rp, ci, val, self._part, P, gamma, kind, prec, m,
+                                oras_alpha, C.byref(h))
+        self.setup_s = time.perf_counter() - t0
+        if rc:
+            raise OracleError(f"ras setup: {rc}")
+        self._h = h
+
+    def iterate(self, b, x, tol: float = 0.0, max_iter: int = 1, nthreads: int = 1,
+                allow_noconv: bool = True):
+        """Runs at most max_iter iterations from x (updated in place, float64
+        C-contiguous). Returns (iterations, relres_history)."""
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"] and x.size == self.n
+        hist = np.zeros(max_iter + 1)
+        it = C.c_int32(0)
+        rc = _load().or_ras_iterate(self._h, np.ascontiguousarray(b, dtype=np.float64), tol,
+                                    max_iter, nthreads, x, hist.ctypes.data, C.byref(it))
+        if rc and not (rc == ENOCONV and allow_noconv):
+            raise OracleError(f"ras iterate: {rc}")
+        return it.value, hist[: it.value + 1].copy()
+
+    def close(self):
+        if self._h:
+            _load().or_ras_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+from .direct import (  # noqa: E402,F401
+    band_direct_solve,
+    poisson2d_direct,
+    poisson3d_direct,
+)

@@ -830,52 +830,96 @@ int or_ras_sync(int n, const int32_t *rp, const int32_t *ci, const double *val, 
                         nthreads, x, hist, iters);
 }
 
-int or_ras_sync_ex(int n, const int32_t *rp, const int32_t *ci, const double *val,
-                   const double *b, const int32_t *part, int P, int gamma, int kind, int prec,
-                   int m, double alpha, double tol, int max_iter, int nthreads, double *x,
-                   double *hist, int32_t *iters) {
-  if (n <= 0 || P <= 0 || gamma < 0 || max_iter < 0 || !isfinite(alpha)) return OR_EINVAL;
+/* The set-up half of Algorithm 1 (initialization_and_setup): overlap maps,
+ * local matrices and their factorisations for every subdomain, kept for
+ * or_ras_iterate. Time spent here is not part of the solve (Sec. 3.1). */
+struct or_ras {
+  int n, P, kind, prec, m;
+  const int32_t *rp, *ci;
+  const double *val;
+  or_sub *subs;
+};
+
+int or_ras_new(int n, const int32_t *rp, const int32_t *ci, const double *val,
+               const int32_t *part, int P, int gamma, int kind, int prec, int m, double alpha,
+               or_ras **out) {
+  *out = NULL;
+  if (n <= 0 || P <= 0 || gamma < 0 || !isfinite(alpha)) return OR_EINVAL;
   if (kind < OR_BANDCHOL || kind > OR_GMRES || prec < OR_FP64 || prec > OR_BF16) return OR_EINVAL;
   if (prec == OR_BF16 && kind != OR_BANDCHOL && kind != OR_BANDLU) return OR_EINVAL;
   for (int i = 0; i < n; ++i)
     if (part[i] < 0 || part[i] >= P) return OR_EINVAL;
-  or_sub *subs = (or_sub *)calloc(P, sizeof(or_sub));
+  or_ras *h = (or_ras *)calloc(1, sizeof(or_ras));
+  h->n = n; h->P = P; h->kind = kind; h->prec = prec; h->m = m;
+  h->rp = rp; h->ci = ci; h->val = val;
+  h->subs = (or_sub *)calloc(P, sizeof(or_sub));
   int32_t *g2l = (int32_t *)malloc(sizeof(int32_t) * n);
   for (int i = 0; i < n; ++i) g2l[i] = -1;
   int rc = OR_OK;
   for (int p = 0; p < P && rc == OR_OK; ++p)
-    rc = or_sub_setup(n, rp, ci, val, part, P, p, gamma, kind, alpha, g2l, &subs[p]);
+    rc = or_sub_setup(n, rp, ci, val, part, P, p, gamma, kind, alpha, g2l, &h->subs[p]);
   free(g2l);
+  if (rc != OR_OK) {
+    or_ras_free(h);
+    return rc;
+  }
+  *out = h;
+  return OR_OK;
+}
+
+void or_ras_free(or_ras *h) {
+  if (!h) return;
+  for (int p = 0; p < h->P; ++p) or_sub_free(&h->subs[p]);
+  free(h->subs);
+  free(h);
+}
+
+/* The solve half: synchronous RAS iterations in correction form from x. */
+int or_ras_iterate(const or_ras *h, const double *b, double tol, int max_iter, int nthreads,
+                   double *x, double *hist, int32_t *iters) {
+  if (max_iter < 0) return OR_EINVAL;
+  const int n = h->n, P = h->P;
   double *r = (double *)malloc(sizeof(double) * n);
   double *xn = (double *)malloc(sizeof(double) * n);
   double b2 = 0.0;
   for (int i = 0; i < n; ++i) b2 += b[i] * b[i];
   double bn = sqrt(b2);
-  int k = 0;
-  if (rc == OR_OK) {
-    for (k = 0;; ++k) {
-      double r2 = or_residual(n, rp, ci, val, b, x, r);
-      if (hist) hist[k] = bn > 0.0 ? sqrt(r2) / bn : sqrt(r2);
-      if (r2 < tol * tol * b2) break;
-      if (k == max_iter) { rc = OR_ENOCONV; break; }
+  int rc = OR_OK, k = 0;
+  for (k = 0;; ++k) {
+    double r2 = or_residual(n, h->rp, h->ci, h->val, b, x, r);
+    if (hist) hist[k] = bn > 0.0 ? sqrt(r2) / bn : sqrt(r2);
+    if (r2 < tol * tol * b2) break;
+    if (k == max_iter) { rc = OR_ENOCONV; break; }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-      for (int p = 0; p < P; ++p) {
-        const or_sub *s = &subs[p];
-        double *loc = (double *)malloc(sizeof(double) * (s->no > 0 ? s->no : 1));
-        for (int t = 0; t < s->no; ++t) loc[t] = r[s->omega[t]];
-        or_sub_solve(s, kind, prec, m, loc);
-        for (int t = 0; t < s->no; ++t)
-          if (s->owned[t]) xn[s->omega[t]] = x[s->omega[t]] + loc[t];
-        free(loc);
-      }
-      memcpy(x, xn, sizeof(double) * n);
+    for (int p = 0; p < P; ++p) {
+      const or_sub *s = &h->subs[p];
+      double *loc = (double *)malloc(sizeof(double) * (s->no > 0 ? s->no : 1));
+      for (int t = 0; t < s->no; ++t) loc[t] = r[s->omega[t]];
+      or_sub_solve(s, h->kind, h->prec, h->m, loc);
+      for (int t = 0; t < s->no; ++t)
+        if (s->owned[t]) xn[s->omega[t]] = x[s->omega[t]] + loc[t];
+      free(loc);
     }
+    memcpy(x, xn, sizeof(double) * n);
   }
   *iters = k;
-  for (int p = 0; p < P; ++p) or_sub_free(&subs[p]);
-  free(subs); free(r); free(xn);
+  free(r); free(xn);
   (void)nthreads;
+  return rc;
+}
+
+int or_ras_sync_ex(int n, const int32_t *rp, const int32_t *ci, const double *val,
+                   const double *b, const int32_t *part, int P, int gamma, int kind, int prec,
+                   int m, double alpha, double tol, int max_iter, int nthreads, double *x,
+                   double *hist, int32_t *iters) {
+  *iters = 0;
+  if (max_iter < 0) return OR_EINVAL;
+  or_ras *h = NULL;
+  int rc = or_ras_new(n, rp, ci, val, part, P, gamma, kind, prec, m, alpha, &h);
+  if (rc != OR_OK) return rc;
+  rc = or_ras_iterate(h, b, tol, max_iter, nthreads, x, hist, iters);
+  or_ras_free(h);
   return rc;
 }

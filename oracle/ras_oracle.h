@@ -108,4 +108,19 @@ int or_ras_sync_ex(int n, const int32_t *rp, const int32_t *ci, const double *va
                    int m, double alpha, double tol, int max_iter, int nthreads, double *x,
                    double *hist, int32_t *iters);
 
+/*
+ * The same iteration split as Algorithm 1 splits it: or_ras_new does the
+ * set-up (overlap maps, local matrices, factorisations; untimed in Sec. 3.1)
+ * and keeps pointers to rp / ci / val (which must outlive the handle);
+ * or_ras_iterate runs synchronous RAS iterations from x (the same arithmetic
+ * as or_ras_sync_ex, which is new + iterate + free).
+ */
+typedef struct or_ras or_ras;
+int or_ras_new(int n, const int32_t *rp, const int32_t *ci, const double *val,
+               const int32_t *part, int P, int gamma, int kind, int prec, int m, double alpha,
+               or_ras **out);
+int or_ras_iterate(const or_ras *h, const double *b, double tol, int max_iter, int nthreads,
+                   double *x, double *hist, int32_t *iters);
+void or_ras_free(or_ras *h);
+
 #endif

@@ -679,3 +679,137 @@ def test_residual_vs_scipy():
     rs = b - A.to_scipy() @ x
     assert np.allclose(r, rs, rtol=0, atol=1e-14)
     assert abs(rn - np.linalg.norm(rs)) <= 1e-13 * rn
+
+
+# ---------------------------------------------------------------- FP32 local solvers, bit for bit
+
+def _f32_spmv(A, vals32, p):
+    f = np.float32
+    q = np.zeros(A.n, f)
+    for i in range(A.n):
+        s = f(0)
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            s = f(s + f(vals32[k] * p[A.col[k]]))
+        q[i] = s
+    return q
+
+
+def _f32_dot(a, b):
+    f = np.float32
+    s = f(0)
+    for i in range(a.size):
+        s = f(s + f(a[i] * b[i]))
+    return s
+
+
+def _cg_float32(A, rhs, m):
+    """Textbook CG (q = A p; alpha = rr/(p.q); d += alpha p; r -= alpha q;
+    beta = rr'/rr; p = r + beta p) in float32 arithmetic with A rounded to
+    float32, sums taken in index order."""
+    f = np.float32
+    v32 = A.val.astype(f)
+    r = rhs.astype(f)
+    p = r.copy()
+    d = np.zeros(A.n, f)
+    rr = _f32_dot(r, r)
+    for _ in range(m):
+        if rr == f(0):
+            break
+        q = _f32_spmv(A, v32, p)
+        alpha = f(rr / _f32_dot(p, q))
+        d = (d + alpha * p).astype(f)
+        r = (r - alpha * q).astype(f)
+        rr2 = _f32_dot(r, r)
+        beta = f(rr2 / rr)
+        p = (r + beta * p).astype(f)
+        rr = rr2
+    return d.astype(np.float64)
+
+
+def _ilu_apply_float32(A, lu32, r):
+    """z = U^{-1} L^{-1} r (L unit lower, U upper from the ILU(0) factors)."""
+    f = np.float32
+    n = A.n
+    z = np.zeros(n, f)
+    for i in range(n):
+        s = r[i]
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col[k] >= i:
+                break
+            s = f(s - f(lu32[k] * z[A.col[k]]))
+        z[i] = s
+    for i in range(n - 1, -1, -1):
+        s, dg = z[i], f(0)
+        for k in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            c = A.col[k]
+            if c > i:
+                s = f(s - f(lu32[k] * z[c]))
+            elif c == i:
+                dg = lu32[k]
+        z[i] = f(s / dg)
+    return z
+
+
+def _pcg_ilu0_float32(A, lu, rhs, m):
+    """ILU(0)-preconditioned CG (z = M^{-1} r; p = z; alpha = rz/(p.Ap);
+    d += alpha p; r -= alpha Ap; z = M^{-1} r; beta = rz'/rz; p = z + beta p)
+    in float32 arithmetic with A and the factors rounded to float32."""
+    f = np.float32
+    v32 = A.val.astype(f)
+    lu32 = lu.astype(f)
+    r = rhs.astype(f)
+    d = np.zeros(A.n, f)
+    z = _ilu_apply_float32(A, lu32, r)
+    p = z.copy()
+    rz = _f32_dot(r, z)
+    for _ in range(m):
+        if rz == f(0):
+            break
+        q = _f32_spmv(A, v32, p)
+        alpha = f(rz / _f32_dot(p, q))
+        d = (d + alpha * p).astype(f)
+        r = (r - alpha * q).astype(f)
+        z = _ilu_apply_float32(A, lu32, r)
+        rz2 = _f32_dot(r, z)
+        beta = f(rz2 / rz)
+        p = (z + beta * p).astype(f)
+        rz = rz2
+    return d.astype(np.float64)
+
+
+@pytest.mark.parametrize("m", [1, 3, 7])
+def test_cg_fp32_mode_is_float32_arithmetic(m):
+    # the oracle's FP32 CG equals plain float32 arithmetic bit for bit, and
+    # differs from its FP64 CG (it really rounds)
+    N = 7
+    A = problems.diffusion2d(N, problems.grf_coefficient(N, 5))
+    r = problems.rhs_uniform(A.n, 21)
+    d32 = oracle.cg(A, r, m, oracle.FP32)
+    assert np.array_equal(d32, _cg_float32(A, r, m))
+    assert not np.array_equal(d32, oracle.cg(A, r, m))
+
+
+@pytest.mark.parametrize("m", [1, 3, 6])
+def test_pcg_ilu0_fp32_mode_is_float32_arithmetic(m):
+    # the FP32 branch of the ILU(0)-PCG (factors rounded to float32, both
+    # triangular sweeps and every CG operation in float32) equals plain
+    # float32 arithmetic bit for bit
+    N = 6
+    A = problems.diffusion2d(N, problems.grf_coefficient(N, 3))
+    r = problems.rhs_uniform(A.n, 17)
+    lu = oracle.ilu0(A)
+    d32 = oracle.pcg_ilu0(A, lu, r, m, oracle.FP32)
+    assert np.array_equal(d32, _pcg_ilu0_float32(A, lu, r, m))
+    d64 = oracle.pcg_ilu0(A, lu, r, m)
+    err = np.linalg.norm(d32 - d64) / np.linalg.norm(d64)
+    assert 1e-10 < err < 1e-5
+
+
+def test_pcg_ilu0_fp32_3d_pattern():
+    # the 7-point pattern of config 3's local solver
+    A = problems.poisson3d(4)
+    r = problems.rhs_uniform(A.n, 23)
+    lu = oracle.ilu0(A)
+    for m in (2, 5):
+        assert np.array_equal(oracle.pcg_ilu0(A, lu, r, m, oracle.FP32),
+                              _pcg_ilu0_float32(A, lu, r, m))
