@@ -9,8 +9,9 @@ convergence tests); the plain synchronous FP64 solver and the other variants
 are reported beside it.
 
 --impl reference runs the CPU oracle (sequential FP64 synchronous RAS with the
-same local solver) on the host cores: each step is a bounded sample of
-iterations, extrapolated to the oracle's iteration count for this workload
+same local solver) on the host cores: set up once (untimed, reported), then
+each step is a bounded sample of iterations, whose per-iteration time is
+extrapolated to the oracle's iteration count for this workload
 (tests/golden/config2_sync_fp64_cg20_iterations.txt, written by the oracle).
 """
 from __future__ import annotations
@@ -72,22 +73,57 @@ def oracle_iterations():
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_sample(A, b, part, budget_s: float, nthreads: int):
-    """Times the oracle's sync RAS on a bounded number of iterations; returns
-    (seconds per iteration, iterations run)."""
+def oracle_setup(A, part):
+    """The oracle's set-up half of Algorithm 1 for the benchmark workload
+    (overlap maps, local matrices; sync FP64 RAS with local CG-20), timed
+    apart from the iterations as Sec. 3.1 times its solves."""
     import oracle
 
-    k = 1
+    return oracle.RasSetup(A, part, PX * PX, GAMMA, oracle.CG, oracle.FP64, M_INNER)
+
+
+def oracle_sample(h, b, x, budget_s: float, nthreads: int):
+    """Times the oracle's synchronous RAS iterations on the already set-up
+    handle h, continuing from x (updated in place): one iteration, then as
+    many as fit in the rest of budget_s in one call. Returns (seconds per
+    iteration, iterations run). The per-iteration cost does not depend on the
+    sample length: set-up is excluded and every iteration does the same work."""
     t0 = time.perf_counter()
-    oracle.ras_sync(A, b, part, PX * PX, GAMMA, oracle.CG, oracle.FP64, M_INNER, tol=0.0,
-                    max_iter=k, nthreads=nthreads, allow_noconv=True)
+    h.iterate(b, x, max_iter=1, nthreads=nthreads)
     t1 = time.perf_counter() - t0
-    k2 = max(1, int(budget_s / max(t1, 1e-3)) - 1)
+    k2 = max(1, int((budget_s - t1) / max(t1, 1e-4)))
     t0 = time.perf_counter()
-    oracle.ras_sync(A, b, part, PX * PX, GAMMA, oracle.CG, oracle.FP64, M_INNER, tol=0.0,
-                    max_iter=k2, nthreads=nthreads, allow_noconv=True)
+    h.iterate(b, x, max_iter=k2, nthreads=nthreads)
     t2 = time.perf_counter() - t0
-    return (t1 + t2) / (k + k2), k + k2
+    return (t1 + t2) / (1 + k2), 1 + k2
+
+
+def oracle_baseline(A, b, part, budget_s: float):
+    """cpu_baseline: the oracle timed on the host cores, single-threaded and
+    OpenMP-parallel over the subdomains of an iteration on every core,
+    extrapolated from a bounded sample of iterations to the oracle's own
+    iteration count for this workload; set-up timed once, separately."""
+    cores = os.cpu_count() or 1
+    iters = oracle_iterations()
+    h = oracle_setup(A, part)
+    x = np.zeros(A.n)
+    out = {}
+    for label, nt in (("all_cores", cores), ("single_thread", 1)):
+        spi, k = oracle_sample(h, b, x, budget_s / 2, nt)
+        out[label] = {"value": spi * iters * 1e3, "unit": "ms", "cores": nt,
+                      "ms_per_iteration": spi * 1e3, "iterations_sampled": k}
+    h.close()
+    line = dict(out["all_cores"])
+    line.update({
+        "kind": "oracle",
+        "sample": f"{out['all_cores']['iterations_sampled']} (all cores) and "
+                  f"{out['single_thread']['iterations_sampled']} (one thread) sync FP64 RAS "
+                  f"iterations (local CG-20) of the same workload after one untimed set-up, "
+                  f"per-iteration time x the oracle's {iters} iterations to 1e-8",
+        "setup_ms": h.setup_s * 1e3,
+        "single_thread": out["single_thread"],
+    })
+    return line
 
 
 def run_reference(args):
@@ -105,14 +141,18 @@ def run_reference(args):
     part = oracle.partition_regular2d(N_GRID, N_GRID, PX, PX)
     iters = oracle_iterations()
     cores = os.cpu_count() or 1
-    budget = float(os.environ.get("RAS_REF_STEP_S", "8"))
+    budget = float(os.environ.get("RAS_REF_STEP_S", "1.5"))
+    h = oracle_setup(A, part)  # untimed, as in Sec. 3.1
+    x = np.zeros(A.n)
     for _ in range(args.warmup):
-        oracle_sample(A, b, part, budget / 4, cores)
-    vals, samples = [], []
+        oracle_sample(h, b, x, budget / 4, cores)
+    vals, samples, spis = [], [], []
     for _ in range(args.steps):
-        spi, k = oracle_sample(A, b, part, budget, cores)
+        spi, k = oracle_sample(h, b, x, budget, cores)
         vals.append(spi * iters * 1e3)
         samples.append(k)
+        spis.append(spi * 1e3)
+    h.close()
     v = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
@@ -121,8 +161,11 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "mode": "sync", "local_solver": "CG-20",
                    "local_precision": "fp64", "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": f"{statistics.median(samples)} sync RAS iterations per step, "
-                                   f"extrapolated to the oracle's {iters} iterations"},
+                         "sample": f"{statistics.median(samples)} sync RAS iterations per step "
+                                   f"after one untimed set-up ({h.setup_s * 1e3:.0f} ms), "
+                                   f"per-iteration time x the oracle's {iters} iterations",
+                         "setup_ms": h.setup_s * 1e3,
+                         "ms_per_iteration": statistics.median(spis)},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -195,7 +238,8 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
     """Algorithmic bytes of one local update of each subdomain:
     residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p,
     local CG = nnz(A_p) (s_v + 2), once when A_p is staged in shared memory,
-    m times when it is re-read every step; band = 2 n_p (w_p + 1) s_f (the L
+    m times when it is re-read every step; ILU(0)-PCG = 2 nnz(A_p) (s + 2) m
+    (A_p and the factors every step); band = 2 n_p (w_p + 1) s_f (the L
     and L^T, or L and U, bands);
     update = 8 |O_p| written."""
     rp, ci = A.row_ptr, A.col
@@ -214,6 +258,9 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
         res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
         if kind == ras.RAS_LOCAL_CG:
             loc = nnz_p * (prec_bytes + 2) * (1 if staged else m)
+        elif kind == ras.RAS_LOCAL_ILU0_CG:
+            # A_p and the ILU(0) factors (same pattern) read every PCG step
+            loc = 2 * nnz_p * (prec_bytes + 2) * m
         elif kind in (ras.RAS_LOCAL_BANDCHOL, ras.RAS_LOCAL_BANDLU):
             # local half-bandwidth of A_p in ascending global order
             loc_col = np.searchsorted(om, ci[idx])
@@ -334,12 +381,13 @@ def run_ours(args):
     relres = ras.ras_relres(ctxs[head_prec], bd, x)
 
     # other variants, one solve each
-    var_out = {}
+    var_out, var_x = {}, {"async_fp32": x.cpu().numpy()}
     if not args.quick:
         for name, (mode, prec) in variants.items():
             if name == "async_fp32":
                 continue
-            t, info, _ = solve(mode, prec)
+            t, info, xv = solve(mode, prec)
+            var_x[name] = xv.cpu().numpy()
             var_out[name] = {"ms": t, "status": info.status, "iterations": info.iterations,
                              "updates_median": info.updates_median, "relres": info.relres,
                              "kernel_ms": info.kernel_ms}
@@ -349,7 +397,7 @@ def run_ours(args):
     if not args.quick:
         bh = torch.tensor(b).pin_memory()
         e2e_t, e2e_failed = [], 0
-        for _ in range(args.steps):
+        for _ in range(min(args.steps, 5)):
             xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
             flush.fill_(1.0)
             torch.cuda.synchronize()
@@ -363,7 +411,7 @@ def run_ours(args):
         e2e_v = max_over_ranks(statistics.median(e2e_t) if e2e_t else float("inf"), dev)
         e2e = {"value": e2e_v if e2e_v != float("inf") else None, "unit": "ms",
                "h2d_bytes_per_step": 2 * 8 * A.n, "d2h_bytes_per_step": 8 * A.n,
-               "failed_steps": e2e_failed}
+               "failed_steps": e2e_failed, "steps": len(e2e_t) + e2e_failed}
 
     # roofline of the persistent kernel
     info = infos[len(infos) // 2]
@@ -383,17 +431,21 @@ def run_ours(args):
             "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 
-    band4 = nonsym = oras = None
+    sections = {}
     if not args.quick and world == 1:
-        band4 = band_config4(dev, stream, args.band_iters)
-        try:
-            nonsym = nonsymmetric(dev, stream)
-        except Exception as e:  # reported, never fatal to the headline line
-            nonsym = {"error": f"{type(e).__name__}: {e}"}
-        try:
-            oras = oras_section(dev, stream)
-        except Exception as e:
-            oras = {"error": f"{type(e).__name__}: {e}"}
+        # every section is reported, never fatal to the headline line
+        for name, fn in (("band_config4", lambda: band_config4(dev, stream, args.band_iters)),
+                         ("config3", lambda: config3_section(dev, stream)),
+                         ("config4", lambda: config4_section(dev, stream)),
+                         ("serving", lambda: serving_section(args)),
+                         ("nonsymmetric", lambda: nonsymmetric(dev, stream)),
+                         ("oras", lambda: oras_section(dev, stream))):
+            if name not in args.sections:
+                continue
+            try:
+                sections[name] = fn()
+            except Exception as e:
+                sections[name] = {"error": f"{type(e).__name__}: {e}"}
 
     launches_per_solve = 5  # init, sysnorm, main, residual, sysnorm (async)
     line = {
@@ -412,24 +464,21 @@ def run_ours(args):
         "gpu_launches": launches_per_solve * args.steps,
         "roofline": roof, "clocks": clocks.summary(),
     }
-    if band4 is not None:
-        line["band_config4"] = band4
-    if nonsym is not None:
-        line["nonsymmetric"] = nonsym
-    if oras is not None:
-        line["oras"] = oras
+    line.update(sections)
+    if "serving" in sections and "async_fp32" in sections["serving"]:
+        sv = sections["serving"]
+        line["serving_p50_p99"] = {
+            k: {"p50_ms": sv[k].get("p50_ms"), "p99_ms": sv[k].get("p99_ms"),
+                "solves_per_s": sv[k].get("solves_per_s"), "rejected": sv[k].get("rejected"),
+                "failed": sv[k].get("failed")}
+            for k in ("async_fp32", "sync_fp64") if k in sv}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
 
-        cores = os.cpu_count() or 1
-        spi, k = oracle_sample(A, b, oracle.partition_regular2d(N_GRID, N_GRID, PX, PX),
-                               float(os.environ.get("RAS_CPU_SAMPLE_S", "12")), cores)
-        iters = oracle_iterations()
-        line["cpu_baseline"] = {"value": spi * iters * 1e3, "unit": "ms", "cores": cores,
-                                "kind": "oracle",
-                                "sample": f"{k} sync FP64 RAS iterations (local CG-20) of the "
-                                          f"same workload, extrapolated to the oracle's {iters} "
-                                          f"iterations to 1e-8"}
+        line["cpu_baseline"] = oracle_baseline(
+            A, b, oracle.partition_regular2d(N_GRID, N_GRID, PX, PX),
+            float(os.environ.get("RAS_CPU_SAMPLE_S", "12")))
+        line["error_vs_oracle"] = oracle_errors(var_x, lambda: oracle.poisson2d_direct(N_GRID, b))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -437,6 +486,190 @@ def run_ours(args):
 
         dist.barrier()
         dist.destroy_process_group()
+
+
+def oracle_errors(xs: dict, direct) -> dict:
+    """Error of every reported result against the oracle's FP64 direct
+    solution x* = A^{-1} b (the RAS fixed point), computed on the host after
+    the timed region: relative 2-norm ||x - x*|| / ||x*|| and element-wise
+    max |x - x*| / max |x*|."""
+    xs_ = direct()
+    nrm, mx = float(np.linalg.norm(xs_)), float(np.abs(xs_).max())
+    out = {"reference": "oracle FP64 direct solve of the global system"}
+    for k, xv in xs.items():
+        out[k] = {"rel_2norm": float(np.linalg.norm(xv - xs_)) / nrm,
+                  "rel_max": float(np.abs(xv - xs_).max()) / mx}
+    return out
+
+
+def _timed_solve(ras, ctx, bd, n, dev, tol, mode, flush, max_updates=0):
+    """One solve from x = 0 after an L2 flush; a solve that stops with an
+    error returns its info (status, error site) instead of raising."""
+    import torch
+
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush.fill_(1.0)  # L2 flush outside the timed region
+    torch.cuda.synchronize()
+    try:
+        info = ras.ras_solve(ctx, bd, x, tol, mode, max_updates)
+    except ras.RasError as err:
+        if err.info is None:
+            raise
+        info = err.info
+    return info, x
+
+
+def _info_row(info):
+    return {"ms": info.solve_ms, "kernel_ms": info.kernel_ms, "status": info.status,
+            "error_site": info.error_site, "grid": info.grid,
+            "iterations": info.iterations,
+            "updates": [info.updates_min, info.updates_median, info.updates_max],
+            "restarts": info.restarts, "relres": info.relres}
+
+
+def config3_section(dev, stream):
+    """Config 3: 3D Poisson 7-point 128^3 (2,097,152 unknowns), b uniform seed
+    3, seeded BFS-growth partition into 512 uneven parts (seed 3), overlap 1,
+    local ILU(0)-PCG in FP32 with FP64 outer residual / update; the launch
+    shape and inner step count picked by ras_autotune, then time to 1e-8
+    synchronous and asynchronous (one solve each, L2 flushed). Roofline: the
+    local solve's model of 2 nnz(A_p) (s + 2) bytes per PCG step (A_p and
+    the ILU(0) factors, SURVEY's 84 m B/row at 7 nnz/row, s = 4) plus the
+    residual rows and owned writes. Errors against the oracle's closed-form
+    FP64 solve."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    N, P = 128, 512
+    A = problems.poisson3d(N)
+    b = problems.rhs_uniform(A.n, 3)
+    t0 = time.perf_counter()
+    part = ras.ras_partition_bfs(A, P, 3)
+    ctx = ras.ras_setup(A, part, P, 1, ras.RAS_LOCAL_ILU0_CG, ras.RAS_FP32, 10, stream=stream)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    bd = torch.tensor(b, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    xs = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    tune = ras.ras_autotune(ctx, xs, ras.RAS_ASYNC, 20, True)
+    tune_ms = (time.perf_counter() - t0) * 1e3
+    launch = ras.ras_get_launch(ctx)
+    out = {"workload": "3D Poisson 7-point 128^3 (2,097,152 unknowns), uniform RHS seed 3, "
+                       "BFS-growth 512 parts (seed 3), overlap 1, ILU(0)-PCG FP32 local solves, "
+                       "FP64 outer, tol 1e-8, autotuned launch",
+           "setup_ms": setup_ms, "autotune_ms": tune_ms,
+           "autotune": {"cta_threads": tune.cta_threads, "inner_iters": tune.inner_iters,
+                        "candidates": tune.candidates}, "launch": launch}
+    peak, peak_src = measured_peaks()
+    xsol = {}
+    for mname, mode in (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)):
+        info, x = _timed_solve(ras, ctx, bd, A.n, dev, TOL, mode, flush)
+        out[mname] = _info_row(info)
+        xsol[mname] = x.cpu().numpy()
+        counts = ras.ras_get_update_counts(ctx)
+        per_upd = subdomain_bytes(A, ras, ctx, ras.RAS_LOCAL_ILU0_CG, 4, launch["inner_iters"],
+                                  False)
+        alg = float(np.dot(counts, per_upd))
+        ach = alg / (info.kernel_ms / 1e3) / 1e9
+        out[mname]["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                  "frac": ach / peak, "peak_source": peak_src,
+                                  "algorithmic_bytes": alg, "traffic": None}
+    ras.ras_destroy(ctx)
+    import oracle
+
+    out["error_vs_oracle"] = oracle_errors(xsol, lambda: oracle.poisson3d_direct(N, b))
+    return out
+
+
+def config4_section(dev, stream):
+    """Config 4: 2D diffusion 2048^2 (4,194,304 unknowns), k = exp(GRF sigma 1,
+    ell 1/32, seed 4), b uniform seed 4, regular 32x32 = 1024 subdomains,
+    overlap 4, banded Cholesky factorised in FP64 and stored in FP32, BF16 or
+    FP64: time to 1e-8, synchronous for every storage precision and
+    asynchronous with FP32 factors (one solve each, L2 flushed). A direct
+    solve of the full system is out of the oracle's reach (a 69 GB band), so
+    the full-size results are compared with each other and their FP64
+    residuals reported; the error against the oracle's FP64 direct solve is
+    taken on the same recipe at 256^2 with the same 64 x 64 subdomains and
+    overlap (4 x 4 parts), where the oracle's banded Cholesky of the whole
+    system is feasible."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+
+    out = {"workload": "2D diffusion 2048x2048 (4,194,304 unknowns), k = exp(GRF sigma 1, ell 1/32, "
+                       "seed 4), uniform RHS seed 4, regular2d 32x32 = 1024 subdomains, overlap 4, "
+                       "banded Cholesky (factors FP64 / FP32 / BF16), tol 1e-8"}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peak, peak_src = measured_peaks()
+    precs = (("fp32", ras.RAS_FP32, 4), ("bf16", ras.RAS_BF16_STORE, 2), ("fp64", ras.RAS_FP64, 8))
+    for n, px in ((2048, 32), (256, 4)):
+        A = problems.diffusion2d(n, problems.grf_coefficient(n, 4))
+        b = problems.rhs_uniform(A.n, 4)
+        part = ras.ras_partition_regular2d(n, n, px, px)
+        bd = torch.tensor(b, device=dev)
+        xsol, rows = {}, {}
+        for name, prec, sb in precs:
+            ctx = ras.ras_setup(A, part, px * px, 4, ras.RAS_LOCAL_BANDCHOL, prec, stream=stream)
+            modes = (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)) if name == "fp32" else \
+                (("sync", ras.RAS_SYNC),)
+            for mname, mode in modes:
+                info, x = _timed_solve(ras, ctx, bd, A.n, dev, TOL, mode, flush)
+                row = _info_row(info)
+                if n == 2048:
+                    counts = ras.ras_get_update_counts(ctx)
+                    per_upd = subdomain_bytes(A, ras, ctx, ras.RAS_LOCAL_BANDCHOL, sb, 1, True)
+                    alg = float(np.dot(counts, per_upd))
+                    ach = alg / (info.kernel_ms / 1e3) / 1e9
+                    row["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak,
+                                       "unit": "GB/s", "frac": ach / peak,
+                                       "peak_source": peak_src, "algorithmic_bytes": alg}
+                rows[f"{mname}_{name}"] = row
+                xsol[f"{mname}_{name}"] = x.cpu().numpy()
+            ras.ras_destroy(ctx)
+        if n == 2048:
+            out.update(rows)
+            ref = xsol["sync_fp64"]
+            nr = float(np.linalg.norm(ref))
+            out["difference_vs_fp64_factors"] = {
+                k: float(np.linalg.norm(v - ref)) / nr for k, v in xsol.items() if k != "sync_fp64"}
+        else:
+            import oracle
+
+            out["error_vs_oracle_256"] = oracle_errors(
+                xsol, lambda: oracle.band_direct_solve(A, b))
+            out["error_vs_oracle_256"]["iterations"] = {k: r["iterations"] for k, r in rows.items()}
+    return out
+
+
+def serving_section(args):
+    """Config 5 in a bounded form: the seeded Poisson-arrival stream of 2D
+    Poisson solves (side uniform in 64..512, 64 x 64 subdomains, overlap 2,
+    banded Cholesky), served by continuous batching. First the saturation
+    throughput of plain sync FP64 (every request present at t = 0); then
+    async mixed precision (FP32 factors) and sync FP64 each on an open-loop
+    stream at 0.8 x that throughput (the 0.8 point of the rates 0.5 / 0.8 /
+    0.95 x saturation). p50 / p99 latency = completion - arrival."""
+    import paper_2003_05361_gb300 as ras
+    from paper_2003_05361_gb300.serve import Server, request_stream
+
+    nsat, nreq = args.serve_sat_requests, args.serve_requests_bench
+    sat_srv = Server(mode=ras.RAS_SYNC, prec=ras.RAS_FP64, step_limit=args.serve_step,
+                     workers=args.serve_workers)
+    sat = sat_srv.run(request_stream(nsat, rate=1e6, seed=7))
+    rate = 0.8 * sat["solves_per_s"]
+    out = {"workload": f"{nreq} seeded Poisson-arrival 2D Poisson solves per arm, side U{{64..512}}, "
+                       f"64x64 subdomains, overlap 2, banded Cholesky, tol 1e-8, rate 0.8 x the "
+                       f"sync-FP64 saturation throughput",
+           "saturation_sync_fp64": {"requests": nsat, "solves_per_s": sat["solves_per_s"],
+                                    "rejected": sat.get("rejected"), "failed": sat.get("failed")},
+           "rate_per_s": rate}
+    for name, mode, prec in (("async_fp32", ras.RAS_ASYNC, ras.RAS_FP32),
+                             ("sync_fp64", ras.RAS_SYNC, ras.RAS_FP64)):
+        srv = Server(mode=mode, prec=prec, step_limit=args.serve_step, workers=args.serve_workers)
+        out[name] = srv.run(request_stream(nreq, rate=rate, seed=5))
+    return out
 
 
 def band_config4(dev, stream, iters: int):
@@ -757,7 +990,14 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-step", type=int, default=20)
     ap.add_argument("--serve-workers", type=int, default=2, help="host threads doing request setup")
+    ap.add_argument("--serve-sat-requests", type=int, default=40,
+                    help="requests of the saturation run in the default benchmark")
+    ap.add_argument("--serve-requests-bench", type=int, default=60,
+                    help="requests per serving arm in the default benchmark")
+    ap.add_argument("--sections", default="band_config4,config3,config4,serving,nonsymmetric,oras",
+                    help="comma-separated extra sections of the default run")
     args = ap.parse_args()
+    args.sections = [x for x in args.sections.split(",") if x]
     if args.sweep:
         run_sweep(args)
     elif args.serve:

@@ -48,7 +48,7 @@ def test_sync_trajectory_matches_oracle(kind, m, alpha, rtol):
         assert info.status == ras.RAS_ENOCONV and info.iterations == k
         xo = oracle.ras_sync(A, b, part, 6, 2, KINDS[kind], oracle.FP64, m, tol=0.0, max_iter=k,
                              allow_noconv=True, oras_alpha=alpha)[0]
-        assert np.linalg.norm(x - xo) <= rtol * np.linalg.norm(xo), k
+        assert np.abs(x - xo).max() <= rtol * np.abs(xo).max(), k
     ras.ras_destroy(ctx)
 
 

@@ -1,9 +1,11 @@
 """GPU parity tests: the CUDA path through the C ABI against the CPU oracle.
 
 Bars (stated per test): index maps and partitions bit-exact; synchronous
-FP64 iterates x^k equal to the oracle's up to rounding (1e-12 relative for
-the banded direct solver, 1e-9 for CG / ILU-PCG whose dot products are
-reduced in a different order); every converged result has a true FP64
+FP64 iterates x^k equal to the oracle's up to rounding, element by element
+(max |x - x_o| <= rtol max |x_o|, rtol 1e-12 for the banded direct solver,
+1e-9 for CG / ILU-PCG whose dot products are reduced in a different order);
+FP32 iterates within 4 x the oracle's own FP32-vs-FP64 gap, element by
+element; every converged result has a true FP64
 relative residual below the tolerance (checked with the oracle's residual)
 and an error against the direct solution within the bound the residual
 implies."""
@@ -80,7 +82,7 @@ def test_config1_sync_band_fp64():
     xo, it, hist = oracle.ras_sync(A, b, part, 4, 2, tol=1e-8)
     assert info.status == 0
     assert abs(info.iterations - it) <= 1
-    assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
     rr = true_relres(A, b, x)
     assert rr < 1e-8 and abs(rr - info.relres) <= 1e-6 * rr
     assert np.linalg.norm(x - u) / np.linalg.norm(u) <= rr * (1 + 1e-6)
@@ -99,7 +101,7 @@ def test_sync_trajectory_matches_oracle(kind, m, rtol):
         assert info.status == ras.RAS_ENOCONV and info.iterations == k
         xo, _ = oracle.ras_sync(A, b, part, 6, 2, OR_KIND[kind], oracle.FP64, max(m, 1), tol=0.0,
                                 max_iter=k, allow_noconv=True)[:2]
-        assert np.linalg.norm(x - xo) <= rtol * np.linalg.norm(xo), k
+        assert np.abs(x - xo).max() <= rtol * np.abs(xo).max(), k
     ras.ras_destroy(ctx)
 
 
@@ -117,7 +119,7 @@ def test_sync_converged_matches_oracle(kind):
     slack = 1 if kind == BAND else max(2, int(0.01 * it))
     assert info.status == 0 and abs(info.iterations - it) <= slack
     assert true_relres(A, b, x) < 1e-8
-    assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+    assert np.abs(x - xo).max() <= 1e-7 * np.abs(xo).max()
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -141,7 +143,11 @@ def test_staged_fp32_cg_iterates_match_oracle_fp32(dim):
         assert info.iterations == k
         xo = oracle.ras_sync(A, b, part, P, 2, oracle.CG, oracle.FP32, 20, tol=0.0, max_iter=k,
                              allow_noconv=True)[0]
-        assert np.linalg.norm(x - xo) <= 2e-4 * np.linalg.norm(xo), k
+        xo64 = oracle.ras_sync(A, b, part, P, 2, oracle.CG, oracle.FP64, 20, tol=0.0,
+                               max_iter=k, allow_noconv=True)[0]
+        gap = np.abs(xo - xo64).max()
+        assert 0.0 < gap <= 1e-4 * np.abs(xo64).max()
+        assert np.abs(x - xo).max() <= 4.0 * gap + 1e-7 * np.abs(xo64).max(), (k, gap)
     ras.ras_destroy(ctx)
 
 
@@ -307,7 +313,7 @@ def test_tiny_subdomains_and_zero_overlap():
         x, info = gpu_solve(A, b, part, 9, gamma, tol=1e-10)
         xo, it, _ = oracle.ras_sync(A, b, part, 9, gamma, tol=1e-10)
         assert info.status == 0 and abs(info.iterations - it) <= 1
-        assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+        assert np.abs(x - xo).max() <= 1e-9 * np.abs(xo).max()
 
 
 def test_max_updates_reports_noconv():
