@@ -821,15 +821,19 @@ def oras_section(dev, stream, max_updates: int = 12000):
 
 
 def run_sweep(args):
-    """One-GPU analogues of the paper's overlap and partitioning experiments
-    (Sec. 4.3-4.5) on the benchmark's 2D Poisson problem (1024^2, b seed 1) in
-    256 subdomains, regular2d 16x16 or seeded BFS growth (seed 1): overlap
-    1 / 2 / 4 / 8 with banded Cholesky local solves in FP32 (the paper's direct
-    local solver; BFS parts exceed its bandwidth limit) and overlap 1 / 2 / 4
-    with CG-20 in FP32, synchronous vs asynchronous; for overlap 4 with the
-    banded solver also the decentralized detection scheme (Sec. 3.3.2). One
-    solve per synchronous point, the median (by time) of 3 per asynchronous
-    point."""
+    """One-GPU analogues of the paper's partitioning and overlap experiments
+    (Sec. 4.2, regular1d vs regular2d vs a graph partitioner; Sec. 4.3,
+    overlap) on the benchmark's 2D Poisson problem (1024^2, b seed 1) in 256
+    subdomains: regular2d 16x16, regular1d (256 strips of 4 rows) and seeded
+    BFS growth (seed 1). Local solvers: banded Cholesky in FP32 (the paper's
+    direct local solver) at overlap 1 / 2 / 4 / 8 / 16 and CG-20 in FP32 at
+    overlap 1 / 2 / 4 / 8; synchronous vs asynchronous, and for overlap 4 with
+    the banded solver also the decentralized detection scheme (Sec. 3.3.2).
+    A combination outside a local solver's limits (local half-bandwidth > 160
+    for the banded solver; a local problem that does not fit in shared
+    memory for CG) is reported as an error row. One solve per synchronous
+    point; asynchronous points are the median (by time) of --sweep-reps
+    solves (10, as Sec. 4.1 averages its runs) with the minimum and maximum."""
     import torch
 
     import paper_2003_05361_gb300 as ras
@@ -838,18 +842,24 @@ def run_sweep(args):
     A, b = problem()
     bd = torch.tensor(b, device="cuda")
     parts = {"regular2d": ras.ras_partition_regular2d(N_GRID, N_GRID, PX, PX),
+             "regular1d": ras.ras_partition_regular2d(N_GRID, N_GRID, 1, PX * PX),
              "bfs": ras.ras_partition_bfs(A, PX * PX, 1)}
-    solvers = {"band_fp32": (ras.RAS_LOCAL_BANDCHOL, 1, (1, 2, 4, 8)),
-               "cg20_fp32": (ras.RAS_LOCAL_CG, M_INNER, (1, 2, 4))}
+    solvers = {"band_fp32": (ras.RAS_LOCAL_BANDCHOL, 1, (1, 2, 4, 8, 16)),
+               "cg20_fp32": (ras.RAS_LOCAL_CG, M_INNER, (1, 2, 4, 8))}
     rows = []
 
     def run(ctx, mode, reps):
         out = []
         for _ in range(reps):
             x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-            out.append(ras.ras_solve(ctx, bd, x, TOL, mode))
+            try:
+                out.append(ras.ras_solve(ctx, bd, x, TOL, mode))
+            except ras.RasError as err:
+                if err.info is None:
+                    raise
+                out.append(err.info)
         out.sort(key=lambda i: i.kernel_ms)
-        return out[len(out) // 2]
+        return out[len(out) // 2], [i.kernel_ms for i in out], sum(i.status != 0 for i in out)
 
     for pname, part in parts.items():
         for sname, (kind, m, gammas) in solvers.items():
@@ -861,19 +871,21 @@ def run_sweep(args):
                     rows.append(row)
                     print(json.dumps(row), flush=True)
                     continue
-                modes = [("sync", ras.RAS_SYNC, 1), ("async", ras.RAS_ASYNC, 3)]
+                modes = [("sync", ras.RAS_SYNC, 1), ("async", ras.RAS_ASYNC, args.sweep_reps)]
                 if gamma == 4 and kind == ras.RAS_LOCAL_BANDCHOL:
-                    modes.append(("async_decentral", ras.RAS_ASYNC_DECENTRAL, 3))
+                    modes.append(("async_decentral", ras.RAS_ASYNC_DECENTRAL, args.sweep_reps))
                 for mname, mode, reps in modes:
-                    info = run(ctx, mode, reps)
+                    info, all_ms, nfail = run(ctx, mode, reps)
                     ph = ras.ras_get_phase_times(ctx).astype(np.float64)
                     upd = np.maximum(ras.ras_get_update_counts(ctx), 1).astype(np.float64)
                     per = (ph / upd[:, None]).mean(0) / 1e3
                     row = {"partition": pname, "local": sname, "overlap": gamma, "mode": mname,
                            "status": info.status, "ms": info.kernel_ms,
+                           "ms_min": min(all_ms), "ms_max": max(all_ms), "runs": reps,
+                           "failed_runs": nfail,
                            "iterations": info.iterations, "updates_min": info.updates_min,
                            "updates_max": info.updates_max, "restarts": info.restarts,
-                           "relres": info.relres,
+                           "relres": info.relres, "grid": info.grid,
                            "us_per_update": {"gather": per[0], "solve": per[1], "update": per[2]},
                            "max_local_bandwidth": int(ras.ras_get_info(ctx)["max_bandwidth"])}
                     if mode != ras.RAS_SYNC:
@@ -985,6 +997,8 @@ def main():
                     help="sync iterations of the config-4 band roofline launch")
     ap.add_argument("--sweep", action="store_true",
                     help="overlap / partition / detection sweep on the benchmark problem")
+    ap.add_argument("--sweep-reps", type=int, default=10,
+                    help="asynchronous solves per sweep point (median, min, max)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload only")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=20.0)

@@ -131,7 +131,9 @@ typedef struct {
   int32_t error_site;     /* RAS_ETIMEOUT only: 1 grid barrier, 3 async idle wait,
                              4 whole-solve time limit, 5 staged-matrix copy (2 is not
                              used: the band copies complete by construction) */
-  int32_t reserved_;
+  int32_t grid;           /* CTAs of the solve's persistent launch (asynchronous
+                             solves take subdomains by ticket on every co-resident
+                             CTA slot; synchronous ones use the static plan) */
 } ras_solve_info;
 
 /* ------------------------------------------------------------------------ */
@@ -293,9 +295,10 @@ ras_status ras_relres(ras_ctx *ctx, const double *b, const double *x, double *re
  * 1 MiB file-scope device array that every GPU loading the library holds
  * until exit, so n may be at most 67,108,864 (larger n: RAS_EINVAL). The
  * first call on a device looks the array's address up with that device
- * current; make that first call before any stream capture. All calls share
- * the array: calls that overlap on the GPU race and must be ordered by the
- * caller. */
+ * current; make that first call before any stream capture (calls outside a
+ * capture look it up again, so a cudaDeviceReset in between does no harm).
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * ordered by the caller. */
 ras_status ras_relres_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                               const double *val, const double *b, const double *x, double *relres,
                               void *cuda_stream);

@@ -44,7 +44,7 @@ class ras_solve_info(C.Structure):
                 ("updates_median", C.c_int64), ("updates_max", C.c_int64),
                 ("relres", C.c_double), ("solve_ms", C.c_double), ("restarts", C.c_int32),
                 ("status", C.c_int32), ("kernel_ms", C.c_double), ("stale_updates", C.c_int64),
-                ("error_site", C.c_int32), ("reserved_", C.c_int32)]
+                ("error_site", C.c_int32), ("grid", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -115,6 +115,43 @@ int64_t env_int(const char *name, int64_t dflt) {
   return std::strtoll(v, nullptr, 10);
 }
 
+// Host-side fault injection for the allocation-failure paths (nothing
+// reaches the GPU): with RAS_FAULT_ALLOC=k (k >= 1) in the environment, the
+// k-th device or pinned-host allocation counted on this thread since the
+// start of the current ras_setup reports cudaErrorMemoryAllocation without
+// allocating. Unset or 0: every call goes to the CUDA runtime.
+thread_local int64_t t_alloc_count = 0;
+bool inject_alloc_failure() {
+  const int64_t k = env_int("RAS_FAULT_ALLOC", 0);
+  return k > 0 && ++t_alloc_count == k;
+}
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+template <typename T> cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T> cudaError_t host_malloc_pinned(T **p, size_t bytes) {
+  if (inject_alloc_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(reinterpret_cast<void **>(p), bytes);
+}
+
+// A temporary device buffer freed when it goes out of scope (setup paths
+// that return early on an error).
+struct TmpDev {
+  void *p = nullptr;
+  ~TmpDev() {
+    if (p) cudaFree(p);
+  }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------- context
@@ -126,6 +163,7 @@ struct DevBuf {
 
 struct LaunchPlan {
   int nt = 0, grid = 0, kmax = 0, nstages = 4;
+  int grid_dyn = 0;  // CTAs of the dynamic asynchronous schedule (all co-resident slots)
   size_t smem = 0;
   int Wmax = 0, npad_max = 0;
   std::vector<Item> items;
@@ -198,7 +236,7 @@ struct ras_ctx {
   ras_status alloc(T *&ptr, size_t count) {
     void *p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_malloc(&p, bytes);
     if (e != cudaSuccess) {
       last_cuda_error() = e;
       return RAS_ENOMEM;
@@ -502,10 +540,13 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   const int64_t per = (nit + cap - 1) / std::max<int64_t>(cap, 1);
   pl.grid = (int)(per > 0 ? (nit + per - 1) / per : 0);
   if (pl.grid <= 0) return RAS_EINVAL;
+  // the dynamic asynchronous schedule takes items by ticket, so it can use
+  // every co-resident slot (e.g. 152 CTAs for 256 subdomains)
+  pl.grid_dyn = (int)std::min<int64_t>(cap, nit);
   assign_items(pl, items, cost, pl.grid);
   auto up = [&](auto *&d, const auto &v) -> cudaError_t {
     using T = typename std::remove_reference<decltype(v)>::type::value_type;
-    cudaError_t e = cudaMalloc((void **)&d, std::max<size_t>(v.size(), 1) * sizeof(T));
+    cudaError_t e = dev_malloc((void **)&d, std::max<size_t>(v.size(), 1) * sizeof(T));
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream);
   };
@@ -697,6 +738,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   for (int p = 0; p < P; ++p)
     if (owned_lists[p].empty()) return RAS_EINVAL;
 
+  t_alloc_count = 0;  // allocation numbering of the fault-injection hook
   std::unique_ptr<ras_ctx> c(new ras_ctx());
   c->stream = (cudaStream_t)cuda_stream;
   c->n = n;
@@ -736,6 +778,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     d.npad = (d.n + 31) / 32 * 32;
     d.n_own = (int32_t)owned_lists[p].size();
     d.W = (std::max(mp.w, 1) + 3) / 4 * 4;  // band records: W a multiple of 4
+    d.w = mp.w;
+    d.rec = banded ? band_rec_entries(mp.w, d.W, 16 / (int)prec_bytes(prec)) : 0;
     d.row_off = rows;
     d.own_off = owns;
     d.fac_off = fac;
@@ -746,7 +790,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     nbrs += d.n_nbr;
     if (banded) {
       if (mp.w > (kind == RAS_LOCAL_BANDLU ? kMaxBandLuW : kMaxBandW)) return RAS_ENOTSUP;
-      fac += 2ll * (d.npad / 32) * 32 * (d.W + 32);  // forward and backward records
+      fac += 2ll * (d.npad / 32) * d.rec;  // forward and backward compact records
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
@@ -952,10 +996,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   if ((st = c->alloc(c->d_xg, (size_t)rows)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_ctl, 1)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_sysdesc, 1)) != RAS_OK) return st;
-  CUDA_TRY(cudaMallocHost(&c->h_sysdesc, sizeof(SysDesc)));
-  CUDA_TRY(cudaMallocHost(&c->h_ctl, sizeof(GridCtl)));
-  CUDA_TRY(cudaMallocHost(&c->h_st, sizeof(SysState)));
-  CUDA_TRY(cudaMallocHost(&c->h_sub, sizeof(SubState) * P));
+  CUDA_TRY(host_malloc_pinned(&c->h_sysdesc, sizeof(SysDesc)));
+  CUDA_TRY(host_malloc_pinned(&c->h_ctl, sizeof(GridCtl)));
+  CUDA_TRY(host_malloc_pinned(&c->h_st, sizeof(SysState)));
+  CUDA_TRY(host_malloc_pinned(&c->h_sub, sizeof(SubState) * P));
   CUDA_TRY(cudaMemsetAsync(c->d_ctl, 0, sizeof(GridCtl), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->d_xalt, 0, sizeof(double) * n, c->stream));
 
@@ -979,14 +1023,19 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         lj.W = d.W;
         lj.K = Kb;
         lj.nb = d.npad / 32;
+        lj.rec = d.rec;
         lj.band_off = band_off[p];
         lj.fac_off = d.fac_off;
         ljobs.push_back(lj);
       }
     }
-    CUDA_TRY(cudaMalloc(&d_band, std::max<size_t>(band.size(), 1) * sizeof(double)));
-    CUDA_TRY(cudaMalloc(&d_jobs, jobs.size() * sizeof(BandJob)));
-    CUDA_TRY(cudaMalloc(&d_ljobs, ljobs.size() * sizeof(LayoutJob)));
+    TmpDev t_band, t_jobs, t_ljobs;  // freed on every return below
+    CUDA_TRY(dev_malloc(&t_band.p, std::max<size_t>(band.size(), 1) * sizeof(double)));
+    CUDA_TRY(dev_malloc(&t_jobs.p, jobs.size() * sizeof(BandJob)));
+    CUDA_TRY(dev_malloc(&t_ljobs.p, ljobs.size() * sizeof(LayoutJob)));
+    d_band = static_cast<double *>(t_band.p);
+    d_jobs = static_cast<BandJob *>(t_jobs.p);
+    d_ljobs = static_cast<LayoutJob *>(t_ljobs.p);
     CUDA_TRY(cudaMemcpyAsync(d_band, band.data(), band.size() * sizeof(double),
                              cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(BandJob),
@@ -995,9 +1044,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
                              cudaMemcpyHostToDevice, c->stream));
     void *d_fac = nullptr;
     const size_t fbytes = std::max<int64_t>(fac, 1) * prec_bytes(prec);
-    cudaError_t e = cudaMalloc(&d_fac, fbytes);
+    cudaError_t e = dev_malloc(&d_fac, fbytes);
     if (e != cudaSuccess) {
-      cudaFree(d_band); cudaFree(d_jobs); cudaFree(d_ljobs);
+      // the copies above read host vectors that outlive them only until return
+      cudaStreamSynchronize(c->stream);
       return RAS_ENOMEM;
     }
     c->bufs.push_back({d_fac, fbytes});
@@ -1009,9 +1059,6 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       e = launch_band_layout(prec, lu, d_ljobs, (int)ljobs.size(), d_band, d_fac, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(d_band);
-    cudaFree(d_jobs);
-    cudaFree(d_ljobs);
     if (e != cudaSuccess) {
       last_cuda_error() = e;
       return RAS_ECUDA;
@@ -1158,7 +1205,7 @@ namespace {
 ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &pl,
                      SysDesc *d_sys, int nsys, GridCtl *d_ctl, GridCtl *h_ctl, int32_t mode,
                      int64_t max_updates, int m, cudaEvent_t ev0, cudaEvent_t ev1,
-                     cudaEvent_t evk0, cudaEvent_t evk1) {
+                     cudaEvent_t evk0, cudaEvent_t evk1, int *grid_out) {
   Launch L{};
   L.sys = d_sys;
   L.nsys = nsys;
@@ -1183,14 +1230,19 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.persist = 1;
   L.kmax = pl.kmax;
   L.nstages = pl.nstages;
+  const int nitems = (int)pl.items.size();
+  L.nitems = nitems;
+  // asynchronous solves run on the dynamic schedule unless RAS_ASYNC_DYNAMIC=0
+  L.dynamic = (mode != RAS_SYNC && env_int("RAS_ASYNC_DYNAMIC", 1) != 0) ? 1 : 0;
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
-  const int nitems = (int)pl.items.size();
   CUDA_TRY(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaEventRecord(ev0, stream));
   CUDA_TRY(launch_init(L, nitems, stream));
   CUDA_TRY(cudaEventRecord(evk0, stream));
-  CUDA_TRY(launch_main(kind, prec, pl.nt, L, pl.grid, pl.smem, stream));
+  const int grid = L.dynamic ? pl.grid_dyn : pl.grid;
+  if (grid_out) *grid_out = grid;
+  CUDA_TRY(launch_main(kind, prec, pl.nt, L, grid, pl.smem, stream));
   CUDA_TRY(cudaEventRecord(evk1, stream));
   if (mode == RAS_SYNC) CUDA_TRY(launch_copyback(L, nitems, stream));
   CUDA_TRY(cudaEventRecord(ev1, stream));
@@ -1199,7 +1251,7 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
 }
 
 ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const SubState *sub,
-                       int32_t mode, ras_solve_info *info, float ms, float kms) {
+                       int32_t mode, ras_solve_info *info, float ms, float kms, int grid) {
   ras_status rs = RAS_OK;
   if (ctl.status != 0) rs = (ras_status)ctl.status;
   else if (st.status != 0) rs = (ras_status)st.status;
@@ -1228,6 +1280,7 @@ ras_status finish_info(ras_ctx *c, const SysState &st, const GridCtl &ctl, const
     info->kernel_ms = kms;
     info->stale_updates = stale;
     info->error_site = ctl.status == RAS_ETIMEOUT ? (int32_t)ctl.err_info : 0;
+    info->grid = grid;
   }
   return rs;
 }
@@ -1241,9 +1294,10 @@ ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t
   *c->h_sysdesc = make_sysdesc(c, b, x, tol);
   CUDA_TRY(cudaMemcpyAsync(c->d_sysdesc, c->h_sysdesc, sizeof(SysDesc), cudaMemcpyHostToDevice,
                            c->stream));
+  int grid = 0;
   ras_status rs = run_solve(c->stream, c->exec_kind, c->ls.prec, c->plan, c->d_sysdesc, 1, c->d_ctl,
                             c->h_ctl, mode, max_updates, c->ls.inner_iters, c->ev0, c->ev1,
-                            c->evk0, c->evk1);
+                            c->evk0, c->evk1, &grid);
   if (rs != RAS_OK) return rs;
   CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream));
@@ -1253,7 +1307,7 @@ ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t
   float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   cudaEventElapsedTime(&kms, c->evk0, c->evk1);
-  return finish_info(c, *c->h_st, *c->h_ctl, c->h_sub, mode, info, ms, kms);
+  return finish_info(c, *c->h_st, *c->h_ctl, c->h_sub, mode, info, ms, kms, grid);
 }
 
 ras_status ras_solve_host(ras_ctx *c, const double *b_host, double *x_host, double tol,
@@ -1318,14 +1372,15 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
     cudaFree(d_ctl);
     pl.release();
   };
-  if (cudaMalloc(&d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
-      cudaMalloc(&d_ctl, sizeof(GridCtl)) != cudaSuccess) {
+  if (dev_malloc(&d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+      dev_malloc(&d_ctl, sizeof(GridCtl)) != cudaSuccess) {
     cleanup();
     return RAS_ENOMEM;
   }
   cudaMemcpyAsync(d_sys, sd.data(), sizeof(SysDesc) * num, cudaMemcpyHostToDevice, stream);
+  int grid = 0;
   rs = run_solve(stream, c0->exec_kind, c0->ls.prec, pl, d_sys, num, d_ctl, &h_ctl, mode,
-                 max_updates, c0->ls.inner_iters, c0->ev0, c0->ev1, c0->evk0, c0->evk1);
+                 max_updates, c0->ls.inner_iters, c0->ev0, c0->ev1, c0->evk0, c0->evk1, &grid);
   if (rs != RAS_OK) {
     cleanup();
     return rs;
@@ -1347,7 +1402,7 @@ ras_status ras_solve_batch(ras_ctx *const *ctxs, int32_t num, const double *cons
   ras_status first = RAS_OK;
   for (int s = 0; s < num; ++s) {
     ras_status r = finish_info(ctxs[s], hst[s], h_ctl, hsub[s].data(), mode,
-                               infos ? &infos[s] : nullptr, ms, kms);
+                               infos ? &infos[s] : nullptr, ms, kms, grid);
     if (first == RAS_OK && r != RAS_OK) first = r;
   }
   return first;
@@ -1450,11 +1505,11 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
       sc.release();
       return rs;
     }
-    if (cudaMalloc(&sc.d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
-        cudaMalloc(&sc.d_ctl, sizeof(GridCtl)) != cudaSuccess ||
-        cudaMallocHost(&sc.h_sys, sizeof(SysDesc) * num) != cudaSuccess ||
-        cudaMallocHost(&sc.h_ctl, sizeof(GridCtl)) != cudaSuccess ||
-        cudaMallocHost(&sc.h_st, sizeof(SysState) * num) != cudaSuccess) {
+    if (dev_malloc(&sc.d_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+        dev_malloc(&sc.d_ctl, sizeof(GridCtl)) != cudaSuccess ||
+        host_malloc_pinned(&sc.h_sys, sizeof(SysDesc) * num) != cudaSuccess ||
+        host_malloc_pinned(&sc.h_ctl, sizeof(GridCtl)) != cudaSuccess ||
+        host_malloc_pinned(&sc.h_st, sizeof(SysState) * num) != cudaSuccess) {
       sc.release();
       return RAS_ENOMEM;
     }
@@ -1561,7 +1616,7 @@ ras_status ras_batch_step(ras_ctx *const *ctxs, int32_t num, int32_t mode, int64
   for (int s : newly) {
     ras_ctx *c = ctxs[s];
     ras_solve_info tmp{};
-    ras_status r = finish_info(c, sc.h_st[s], *sc.h_ctl, c->h_sub, mode, &tmp, 0.f, 0.f);
+    ras_status r = finish_info(c, sc.h_st[s], *sc.h_ctl, c->h_sub, mode, &tmp, 0.f, 0.f, sc.plan.grid);
     if (infos) infos[s] = tmp;
     if (first == RAS_OK && r != RAS_OK) first = r;
   }

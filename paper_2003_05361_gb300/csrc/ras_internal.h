@@ -30,15 +30,92 @@ enum : int32_t { kOK = 0, kEINVAL = 1, kENOMEM = 2, kENOTSPD = 3, kENOCONV = 4, 
 // async per-system phases
 enum : int32_t { kRun = 0, kDrain = 1, kCheck = 2, kDone = 3 };
 
+#ifdef __CUDACC__
+#define RAS_HD __host__ __device__
+#else
+#define RAS_HD
+#endif
+
+// Compact band records (banded Cholesky / LU solves). Rows are grouped in
+// blocks of 32; the record of block K holds, column by column (column-major,
+// lane = row), only the rows [lo, lo + len) of each column that can be
+// non-zero, rounded out to whole 16-byte chunks of G = 16 / sizeof(value)
+// rows. With w the true local half-bandwidth and W >= w the window width (a
+// multiple of 4), the columns of the forward record of block K are
+//   c in [0, 32):   column c of L_KK^{-1} (lower triangle: rows >= c);
+//   c in [32, 64):  column c-32 of M_K = L_KK^{-1} L[K rows, block K-1] (dense,
+//                   or empty where the band does not reach: c-32 < 32-w);
+//   c in [64, 32+W): the rows of L of block K+1 in the columns of its window
+//                   left of block K, L[32K+32+l][32K+32-W+k], k = c-64
+//                   (rows l <= k - (W-w));
+// and of the backward record of block K (U = L^T for Cholesky, U for LU):
+//   c in [0, 32):   column c of U_KK^{-1} (upper triangle: rows <= c);
+//   c in [32, 64):  column c-32 of M'_K = U_KK^{-1} U[K rows, block K+1] (dense,
+//                   or empty for c-32 > w-1);
+//   c in [64, 32+W): the rows of U of block K-1 in the columns of its window
+//                   right of block K, U[32K-32+l][32K+32+k], k = c-64
+//                   (rows l >= k + 64 - w).
+// The chained solve then needs, per block, the band's own non-zeros (plus the
+// 32 x 32 near-block product) and no dense 32 x (32 + W) operator.
+struct BandCol {
+  int32_t lo, len;
+};
+RAS_HD inline BandCol band_col(int c, int dir, int w, int W, int G) {
+  BandCol r{0, 0};
+  if (c < 32) {
+    if (dir == 0) {
+      r.lo = c / G * G;
+      r.len = 32 - r.lo;
+    } else {
+      const int hi = (c + G) / G * G;  // rows [0, c] rounded up
+      r.len = hi < 32 ? hi : 32;
+    }
+  } else if (c < 64) {
+    // near-block product: column c-32 is zero when the band cannot reach it
+    // (forward: row 32K-32+(c-32) is more than w left of row 32K+31)
+    const int k = c - 32;
+    if (dir == 0 ? k >= 32 - w : k <= w - 1) r.len = 32;
+  } else {
+    const int k = c - 64;
+    if (dir == 0) {
+      const int u = k - (W - w) + 1;  // rows [0, u)
+      if (u > 0) {
+        const int hi = (u + G - 1) / G * G;
+        r.len = hi < 32 ? hi : 32;
+      }
+    } else {
+      const int lo = k + 64 - w;  // rows [lo, 32)
+      if (lo < 32) {
+        r.lo = (lo > 0 ? lo : 0) / G * G;
+        r.len = 32 - r.lo;
+      }
+    }
+  }
+  return r;
+}
+RAS_HD inline int band_ncol(int W) { return 64 + (W > 32 ? W - 32 : 0); }
+// Entries of one record (the same for both directions; the larger is taken).
+RAS_HD inline int band_rec_entries(int w, int W, int G) {
+  int f = 0, b = 0;
+  const int nc = band_ncol(W);
+  for (int c = 0; c < nc; ++c) {
+    f += band_col(c, 0, w, W, G).len;
+    b += band_col(c, 1, w, W, G).len;
+  }
+  return f > b ? f : b;
+}
+
 struct SubDesc {
   int32_t n;        // |Omega_p|
   int32_t npad;     // n rounded up to a multiple of 32
   int32_t n_own;    // |O_p|
   int32_t W;        // band: half-bandwidth w rounded up to a multiple of 4 (>= 4)
+  int32_t w;        // band: true local half-bandwidth
+  int32_t rec;      // band: entries of one compact record (see band_col)
   int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
   int64_t own_off;  // offset into own_l
-  int64_t fac_off;  // band: nb forward records, then nb backward records (32 x (W+32) each)
-                    // (forward from L, backward from U = L^T (Cholesky) or U (LU))
+  int64_t fac_off;  // band: nb forward records, then nb backward records (rec entries
+                    // each; forward from L, backward from U = L^T (Cholesky) or U (LU))
   int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
   int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
   int32_t nlev_f;   // ILU: number of forward / backward levels
@@ -64,7 +141,7 @@ struct SubState {
   int32_t park_epoch;
   int32_t check_epoch;
   int32_t gconv_epoch;  // decentralized detection: epoch of the global flag (-1: none)
-  int32_t pad_;
+  uint32_t busy;        // async, dynamic schedule: 1 while a CTA holds the subdomain
 };
 
 struct SysState {
@@ -153,10 +230,12 @@ struct GridCtl {
   unsigned int count;  // barrier arrivals
   unsigned int gen;    // barrier generation
   int fin_accum;       // systems finished since the last barrier
-  int remaining;       // systems still running (published by the barrier)
+  int remaining;       // systems still running (sync: published by the barrier;
+                       // async: decremented when a system finishes)
   int abort;           // set on any device-side error
   int status;          // first error code
   unsigned long long err_info;
+  unsigned long long ticket;  // async, dynamic schedule: next ticket
 };
 
 struct Launch {
@@ -181,7 +260,9 @@ struct Launch {
   int32_t nstages;             // band: copy pipeline depth in chain steps (4 or 6)
   int32_t fresh;               // async: update only after a neighbour published since the last update
   int32_t consistent;          // async: redo a gather that overlapped a neighbour's write (<= 2 times)
-  int32_t pad3_;
+  int32_t dynamic;             // async, persistent: CTAs take items by ticket (no static assignment)
+  int32_t nitems;              // items in the launch
+  int32_t pad4_;
 };
 
 }  // namespace ras

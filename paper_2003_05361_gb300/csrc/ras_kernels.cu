@@ -66,6 +66,14 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t atom_cas_acquire_u32(uint32_t *p, uint32_t cmp, uint32_t v) {
+  uint32_t old;
+  asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
+               : "=r"(old)
+               : "l"(p), "r"(cmp), "r"(v)
+               : "memory");
+  return old;
+}
 __device__ __forceinline__ int ld_acquire_s32(const int *p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -417,22 +425,25 @@ __global__ void __launch_bounds__(256) band_lu_kernel(const BandJob *jobs, doubl
 // --------------------------------------------------------------------------
 //
 // Rows are grouped in blocks of 32 (K = 0..nb-1; rows >= n are identity rows).
-// With L_KK the diagonal block of the lower factor and W = the local
-// half-bandwidth w, forward substitution block by block is
-//   y_K = L_KK^{-1} (r_K - L_{K,left} y_left) = t_K - M_K y[32K-W, 32K),
-//   t_K = L_KK^{-1} r_K,  M_K = L_KK^{-1} L[K rows, 32K-W .. 32K)   (32 x W)
-// and backward substitution with the upper factor U
-//   z_K = t'_K - M'_K z[32K+32, 32K+32+W),  t'_K = U_KK^{-1} y_K,
-//   M'_K = U_KK^{-1} U[K rows, 32K+32 .. 32K+32+W)                   (32 x W).
+// With L_KK the diagonal block of the lower factor, forward substitution block
+// by block is
+//   y_K = L_KK^{-1} (r_K - L[K rows, block K-1] y_{K-1} - L[K rows, older] y_older)
+//       = L_KK^{-1} t_K - M_K y_{K-1},
+//   t_K = r_K - L[K rows, older] y_older,  M_K = L_KK^{-1} L[K rows, block K-1],
+// where "older" are the window rows [32K - W, 32K - 32) left of block K-1, and
+// backward substitution with the upper factor U mirrors it:
+//   z_K = U_KK^{-1} t'_K - M'_K z_{K+1},  t'_K = y_K - U[K rows, older] z_older,
+//   M'_K = U_KK^{-1} U[K rows, block K+1].
 // Cholesky: L from the band (ld = w+1), U = L^T, so U_KK^{-1} = (L_KK^{-1})^T.
 // LU: unit lower L and U from one band (ld = 2w+1), U_KK inverted on its own.
-// Per subdomain the storage is nb forward records, then nb backward records,
-// each a column-major 32 x (32 + W) matrix (entry (l, j) at j*32 + l):
-//   forward  record K = [ L_KK^{-1} | M_K  ],
-//   backward record K = [ U_KK^{-1} | M'_K ],
-// so that a chain step reads one contiguous record and every one of its
-// 32 + W columns is applied to one broadcast value (the step's own right-hand
-// side for the first 32, a finished window row for the rest).
+// The record of block K holds [inverse diagonal block | M | the older-window
+// rows of the NEXT block of the pass] in the compact column layout of
+// band_col (ras_internal.h): a chain step applies the inverse to t_K and M_K
+// to the previous block, both before one CTA barrier, and accumulates the
+// next block's older-window sum t alongside, so the step still has one
+// barrier while the bytes read are those of the band itself (plus the 32 x 32
+// near-block product). Per subdomain: nb forward records, then nb backward
+// records, jb.rec entries each.
 template <typename T, bool LU>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
@@ -506,35 +517,54 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) Y[LU ? r : 0][m] = col[r];
     __syncwarp();
   }
-  const int64_t rec = (int64_t)32 * (W + 32);
+  // compact records (band_col): forward record K of block K, backward record K
+  constexpr int G = 16 / (int)sizeof(T);
+  const int64_t rec = jb.rec;
   T *F = fac + jb.fac_off + (int64_t)K * rec;
   T *Bk = fac + jb.fac_off + (int64_t)nb * rec + (int64_t)K * rec;
-  for (int m = 0; m < 32; ++m) {
-    F[m * 32 + l] = from_double<T>(X[l][m]);                           // L_KK^{-1}[l][m]
-    Bk[m * 32 + l] = from_double<T>(LU ? Y[LU ? l : 0][m] : X[m][l]);  // U_KK^{-1}[l][m]
+  // entries of the factors, zero outside the band and the matrix
+  auto Lv = [&](int r, int c) -> double {  // lower factor (strictly below the diagonal here)
+    return (r < n && c >= 0 && c < r && r - c <= w) ? at(r, c) : 0.0;
+  };
+  auto Uv = [&](int r, int c) -> double {  // upper factor (strictly right of the diagonal here)
+    if (r < 0 || r >= n || c >= n || c <= r || c - r > w) return 0.0;
+    return LU ? at(r, c) : at(c, r);  // Cholesky: U = L^T
+  };
+  const int ncol = band_ncol(W);
+  int64_t off = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const BandCol bc = band_col(c, 0, w, W, G);
+    if (bc.len == 0) continue;
+    double v;
+    if (c < 32) {
+      v = X[l][c];  // L_KK^{-1}, zero above the diagonal
+    } else if (c < 64) {
+      const int col = 32 * K - 32 + (c - 32);  // near block K-1
+      v = 0.0;
+      for (int m = 0; m <= l; ++m) v += X[l][m] * Lv(32 * K + m, col);
+    } else {
+      v = Lv(32 * K + 32 + l, 32 * K + 32 - W + (c - 64));  // block K+1, left of block K
+    }
+    if (l >= bc.lo && l < bc.lo + bc.len) F[off + (l - bc.lo)] = from_double<T>(v);
+    off += bc.len;
   }
-  // M_K[l][c] = sum_{m <= l} Linv[l][m] L[32K+m][32K-W+c]
-  for (int c = 0; c < W; ++c) {
-    const int col = 32 * K - W + c;
-    double s = 0.0;
-    if (col >= 0)
-      for (int m = 0; m <= l; ++m) {
-        const int r = 32 * K + m;
-        if (r < n && col >= r - w) s += X[l][m] * at(r, col);
-      }
-    F[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
-  }
-  // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c]
-  // (Cholesky: U[a][b] = L[b][a])
-  for (int c = 0; c < W; ++c) {
-    const int r = 32 * K + 32 + c;
-    double s = 0.0;
-    if (r < n)
-      for (int m = l; m < 32; ++m) {
-        const int col = 32 * K + m;
-        if (col >= r - w) s += LU ? Y[LU ? l : 0][m] * at(col, r) : X[m][l] * at(r, col);
-      }
-    Bk[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
+  off = 0;
+  for (int c = 0; c < ncol; ++c) {
+    const BandCol bc = band_col(c, 1, w, W, G);
+    if (bc.len == 0) continue;
+    double v;
+    if (c < 32) {
+      v = LU ? Y[LU ? l : 0][c] : X[c][l];  // U_KK^{-1}, zero below the diagonal
+    } else if (c < 64) {
+      const int col = 32 * K + 32 + (c - 32);  // near block K+1
+      v = 0.0;
+      for (int m = l; m < 32; ++m)
+        v += (LU ? Y[LU ? l : 0][m] : X[m][l]) * Uv(32 * K + m, col);
+    } else {
+      v = Uv(32 * K - 32 + l, 32 * K + 32 + (c - 64));  // block K-1, right of block K
+    }
+    if (l >= bc.lo && l < bc.lo + bc.len) Bk[off + (l - bc.lo)] = from_double<T>(v);
+    off += bc.len;
   }
 }
 
@@ -570,6 +600,7 @@ __global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
     s.park_epoch = -1;
     s.check_epoch = -1;
     s.gconv_epoch = -1;
+    s.busy = 0;
   }
 }
 
@@ -652,70 +683,95 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// Columns of a band record each warp of an NW-warp CTA takes per chain step:
-// ceil((W + 32) / NW) rounded up to a multiple of 4 (W itself is a multiple of
-// 4), so every warp's first column, and the broadcast values it reads, are
-// 16-byte aligned.
-__host__ __device__ inline int band_cols_per_warp(int W, int NW) {
-  return ((W + 32 + NW - 1) / NW + 3) / 4 * 4;
+// Entries of one warp's ring slot in the band chain: an even share of the
+// largest compact record for window Wmax (w = Wmax) plus one straddling
+// column, in whole 16-byte chunks (G values).
+__host__ __device__ inline int band_slot_len(int Wmax, int NW, int G) {
+  const int per = (band_rec_entries(Wmax, Wmax, G) + NW - 1) / NW + 32 + G;
+  return (per + G - 1) / G * G;
 }
 
-// Banded Cholesky solve L L^T delta = r by the whole CTA as two block chains:
-// forward y_K = L_KK^{-1} r_K - M_K y_window, backward
-// z_K = U_KK^{-1} y_K - M'_K z_window. A chain step applies the 32 + W columns
-// of one record (see band_layout_kernel) to broadcast values: column j < 32 to
-// row 32K + j of the step's own input (r in the forward pass, y in the
-// backward pass, read from y before the step overwrites it), window column
-// j = 32 + c to finished row 32K - W + c (forward) or 32K + 32 + c (backward).
-// Warp w takes the contiguous columns [w tw, (w+1) tw) (band_cols_per_warp)
-// and writes its 32 partial sums; after ONE barrier every warp adds the
-// partials in the same fixed order, so all warps hold identical y_K. Window
-// sums enter with a minus sign.
-// Each warp streams its own columns of record s + D - 1 with 16-byte cp.async
-// copies into a private D-slot ring while it computes step s; a copy is waited
-// for by the thread that issued it and published to the warp by __syncwarp,
-// so the chain needs no mbarrier and no second barrier. A slot is refilled one
-// step after it was read, behind that step's barrier. Each warp keeps its own
-// copy of the last 8 finished blocks in win (row g at g & 255, stored twice,
-// at +0 and +256, so that a warp's window rows are one unwrapped run); window
-// rows outside [0, npad) meet zero operator columns and read zero-initialised
-// slots. y[0..npad) holds r on entry and delta on exit; part holds 2 NT
-// partials.
+// Banded Cholesky (or LU) solve L U delta = r by the whole CTA as two block
+// chains over the compact records of band_col (forward with L, backward with
+// U). Step K of the forward pass computes
+//   y_K = L_KK^{-1} t_K - M_K y_{K-1}            (one CTA barrier)
+//   t_{K+1} = r_{K+1} - L[block K+1, older window] y_older
+// where t_K was formed at step K-1; the backward pass mirrors it with U and
+// z. Each warp takes a contiguous run of the record's columns, balanced by
+// stored entries (the run [coff[q0], coff[q1]) is contiguous in memory), and
+// accumulates two partial sums per row: the new block (inverse and near-block
+// columns, applied to the warp's copy of t and to the previous block) and the
+// next block's older-window sum. After the barrier every warp adds the
+// partials of all warps in the same fixed order, so all warps hold identical
+// y_K and t_{K+1}. Copies: each warp streams its own run of record s + D - 1
+// into a private D-slot ring with 16-byte cp.async while it computes step s;
+// a copy is waited for by the thread that issued it (cp.async.wait_group) and
+// published to the warp by __syncwarp, and a slot is refilled one step after
+// it was read. Each warp keeps the last 8 finished blocks in its own ring win
+// (row g at g & 255; rows outside [0, npad) read slots not yet written, which
+// hold zero). y[0..npad) holds r on entry and delta on exit; part holds 4 NT
+// partials, tv 32 values per warp, coff ncol + 1 ints.
 template <typename T, typename CT, int NT, int D>
 __device__ void band_solve_chain(const T *__restrict__ F, const T *__restrict__ Bs, int nb, int W,
-                                 int twm, CT *y, CT *part, CT *win, T *ring) {
+                                 int w, int rec, int slot_len, CT *y, CT *part, CT *win, CT *tv,
+                                 int *coff, T *ring) {
   constexpr int NW = NT / 32;
-  constexpr int V = 16 / (int)sizeof(T);  // values per 16-byte copy
+  constexpr int G = 16 / (int)sizeof(T);  // values per 16-byte copy
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int NI = W + 32;
-  const int tw = band_cols_per_warp(W, NW);
-  const int j0 = warp * tw < NI ? warp * tw : NI;
-  const int j1 = j0 + tw < NI ? j0 + tw : NI;
-  const int cnt = j1 - j0;
-  const int nd = (j1 < 32 ? j1 : 32) - (j0 < 32 ? j0 : 32);  // own-input columns
-  const int nchunk = cnt * 32 / V;  // 16-byte chunks of this warp's columns
-  const int64_t rec = (int64_t)32 * NI;
-  const int slot_len = twm * 32;
+  const int ncol = band_ncol(W);
   T *rw = ring + (size_t)warp * D * slot_len;
-  CT *wy = win + warp * 512;  // two copies of an 8-block ring: reads never wrap
+  CT *wy = win + warp * 256;
+  CT *wt = tv + warp * 32;
   for (int dir = 0; dir < 2; ++dir) {
-    const T *src_l = (dir == 0 ? F : Bs) + (int64_t)j0 * 32 + lane * V;
-    T *dst_l = rw + lane * V;
+    // column offsets of this direction's records: exclusive prefix sums of
+    // the column lengths (warp 0)
+    __syncthreads();  // the previous pass is done with coff
+    if (warp == 0) {
+      int run = 0;
+      for (int c0 = 0; c0 < ncol; c0 += 32) {
+        const int c = c0 + lane;
+        const int len = c < ncol ? band_col(c, dir, w, W, G).len : 0;
+        int v = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        if (c < ncol) coff[c] = run + v - len;
+        run += __shfl_sync(0xffffffffu, v, 31);
+      }
+      if (lane == 0) coff[ncol] = run;
+    }
+    __syncthreads();
+    const int total = coff[ncol];
+    // this warp's columns [q0, q1): the first column at or past its share
+    auto first_at = [&](int target) -> int {
+      for (int c0 = 0; c0 < ncol; c0 += 32) {
+        const int c = c0 + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, c < ncol && coff[c] >= target);
+        if (m) return c0 + __ffs(m) - 1;
+      }
+      return ncol;
+    };
+    const int q0 = warp == 0 ? 0 : first_at((int)((int64_t)total * warp / NW));
+    const int q1 = warp == NW - 1 ? ncol : first_at((int)((int64_t)total * (warp + 1) / NW));
+    const int e0 = coff[q0];
+    const int nchunk = (coff[q1] - e0) / G;
+    const T *src_l = (dir == 0 ? F : Bs) + e0;
     // copies of chain step s into ring slot sl (one commit group, maybe empty)
     auto issue = [&](int s, int sl) {
       if (s < nb) {
-        const T *src = src_l + (dir == 0 ? s : nb - 1 - s) * rec;
-        T *dst = dst_l + sl * slot_len;
-        for (int q0 = 0; q0 < nchunk; q0 += 128) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (q0 + u * 32 + lane < nchunk) cp_async16(dst + (q0 + u * 32) * V, src + (q0 + u * 32) * V);
-        }
+        const T *src = src_l + (int64_t)(dir == 0 ? s : nb - 1 - s) * rec;
+        T *dst = rw + sl * slot_len;
+        for (int q = lane; q < nchunk; q += 32) cp_async16(dst + q * G, src + q * G);
       }
       cp_async_commit();
     };
 #pragma unroll
-    for (int q = 0; q < 16; ++q) wy[q * 32 + lane] = CT(0);
+    for (int q = 0; q < 8; ++q) wy[q * 32 + lane] = CT(0);
+    // t of the first block of the pass (its older window lies outside the
+    // subdomain): r_0 forward, y_{nb-1} backward
+    wt[lane] = y[32 * (dir == 0 ? 0 : nb - 1) + lane];
 #pragma unroll
     for (int s = 0; s < D - 1; ++s) issue(s, s);
     int cur = 0;  // slot of step s
@@ -725,41 +781,39 @@ __device__ void band_solve_chain(const T *__restrict__ F, const T *__restrict__ 
       __syncwarp();
       const int K = dir == 0 ? s : nb - 1 - s;
       const T *sl = rw + cur * slot_len + lane;
-      CT a[4] = {CT(0), CT(0), CT(0), CT(0)};
-      int ii = 0;
-      if (nd > 0) {
-        const CT *ys = y + 32 * K + j0;  // own input rows 32K + j
-        for (; ii < nd; ii += 4) {
-          CT bv[4];
-          ld4(ys + ii, bv);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (ii + u < nd) a[u] += to_ct(sl[(ii + u) * 32]) * bv[u];
-        }
-        ii = nd;
+      // rows of the near block: forward 32K - 32 + k, backward 32K + 32 + k;
+      // of the next block's older window: forward 32K + 32 - W + k, backward
+      // 32K + 32 + k
+      const int nbase = dir == 0 ? 32 * K - 64 : 32 * K;
+      const int obase = dir == 0 ? 32 * K + 32 - W - 64 : 32 * K + 32 - 64;
+      CT a0 = CT(0), a1 = CT(0), ao = CT(0);
+      int off = 0;
+      for (int c = q0; c < q1; ++c) {
+        const BandCol bc = band_col(c, dir, w, W, G);
+        if (bc.len == 0) continue;
+        const int r = lane - bc.lo;
+        const CT v = (r >= 0 && r < bc.len) ? to_ct(sl[off - bc.lo]) : CT(0);
+        off += bc.len;
+        if (c < 32) a0 += v * wt[c];
+        else if (c < 64) a1 -= v * wy[(nbase + c) & 255];
+        else ao -= v * wy[(obase + c) & 255];
       }
-      if (ii < cnt) {
-        // window row of column j: 32K - W - 32 + j (forward), 32K + j (backward)
-        const int g0 = (dir == 0 ? 32 * K - W - 32 : 32 * K) + j0;
-        const CT *ws = wy + (g0 & 255);
-        for (; ii < cnt; ii += 4) {
-          CT bv[4];
-          ld4(ws + ii, bv);
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (ii + u < cnt) a[u] -= to_ct(sl[(ii + u) * 32]) * bv[u];
-        }
-      }
-      CT *pb = part + (s & 1) * NT;
-      pb[warp * 32 + lane] = (a[0] + a[1]) + (a[2] + a[3]);
+      CT *pb = part + (s & 1) * 2 * NT;
+      pb[warp * 32 + lane] = a0 + a1;
+      pb[NT + warp * 32 + lane] = ao;
       __syncthreads();
-      // every warp forms the same y_K
-      CT v = CT(0);
+      // every warp forms the same y_K and t of the next block
+      CT v = CT(0), o = CT(0);
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v += pb[w * 32 + lane];
+      for (int q = 0; q < NW; ++q) {
+        v += pb[q * 32 + lane];
+        o += pb[NT + q * 32 + lane];
+      }
       wy[(K & 7) * 32 + lane] = v;
-      wy[256 + (K & 7) * 32 + lane] = v;
       if (warp == 0) y[32 * K + lane] = v;
+      const int Kn = dir == 0 ? K + 1 : K - 1;
+      if (Kn >= 0 && Kn < nb) wt[lane] = y[32 * Kn + lane] + o;
+      __syncwarp();
       cur = cur + 1 == D ? 0 : cur + 1;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -1340,19 +1394,23 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
-  // band: copy rings | y | partials | window rings ; cg: r p q d ; ilu: r z p q d ;
+  // band: copy rings | y | partials | window rings | t | column offsets ;
+  // cg: r p q d ; ilu: r z p q d ;
   // staged cg: A_p values | A_p columns | p ; gmres: r w v d | GmresSmem
-  static __host__ __device__ int band_twm(int Wmax) { return band_cols_per_warp(Wmax, NT / 32); }
+  static constexpr int G = 16 / (int)sizeof(T);
+  static __host__ __device__ int band_slot(int Wmax) { return band_slot_len(Wmax, NT / 32, G); }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
     return ((size_t)npad_max + 31) / 32 * 32;
   }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
   static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax, int nstages) {
     if (KIND == kBand) {
-      size_t b = (size_t)(NT / 32) * nstages * band_twm(Wmax) * 32 * sizeof(T);  // copy rings
+      size_t b = (size_t)(NT / 32) * nstages * band_slot(Wmax) * sizeof(T);  // copy rings
       b += ylen(Wmax, npad_max) * sizeof(CT);     // y (r / delta)
-      b += 2 * NT * sizeof(CT);                   // partials, two buffers
-      b += (size_t)(NT / 32) * 512 * sizeof(CT);  // per-warp window rings (two copies)
+      b += 4 * NT * sizeof(CT);                   // partials: two buffers x two sums
+      b += (size_t)(NT / 32) * 256 * sizeof(CT);  // per-warp window rings
+      b += (size_t)(NT / 32) * 32 * sizeof(CT);   // per-warp t
+      b += ((size_t)band_ncol(Wmax) + 1 + 3) / 4 * 4 * sizeof(int);  // column offsets
       return b;
     }
     if (KIND == kCGS) {
@@ -1381,6 +1439,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   __shared__ double s_red[NT / 32 * 2];
   __shared__ __align__(16) CT s_redc[4 * (NT / 32)];
   __shared__ int s_flag[8];
+  __shared__ int s_dyn[2];
   __shared__ uint32_t s_seq[32];  // async: neighbours' sequence values seen before the gather
   __shared__ __align__(8) uint64_t s_mbar[1];
   __shared__ int s_done[kMaxCtaSys];
@@ -1388,20 +1447,26 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
 
   const int tid = threadIdx.x;
   const int c = blockIdx.x;
-  const int i0 = L.cta_off[c], i1 = L.cta_off[c + 1];
-  const int cs0 = L.cta_sys_off[c], cs1 = L.cta_sys_off[c + 1];
+  // static schedule: this CTA's items [i0, i1) and systems [cs0, cs1); the
+  // dynamic schedule (more CTAs than the static plan) uses neither
+  const bool dyn = L.dynamic != 0;
+  const int i0 = dyn ? 0 : L.cta_off[c], i1 = dyn ? 0 : L.cta_off[c + 1];
+  const int cs0 = dyn ? 0 : L.cta_sys_off[c], cs1 = dyn ? 0 : L.cta_sys_off[c + 1];
   const int nls = cs1 - cs0;
 
   // shared-memory carve-up
   T *ring = nullptr;
   CT *ybuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
-     *v4 = nullptr, *wbuf = nullptr, *gsm = nullptr;
-  const int twm = SM::band_twm(L.Wmax);
+     *v4 = nullptr, *wbuf = nullptr, *tvbuf = nullptr, *gsm = nullptr;
+  int *coffbuf = nullptr;
+  const int slot_len = KIND == kBand ? SM::band_slot(L.Wmax) : 0;
   if (KIND == kBand) {
     ring = reinterpret_cast<T *>(smem);
-    ybuf = reinterpret_cast<CT *>(smem + (size_t)(NT / 32) * L.nstages * twm * 32 * sizeof(T));
+    ybuf = reinterpret_cast<CT *>(smem + (size_t)(NT / 32) * L.nstages * slot_len * sizeof(T));
     pbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
-    wbuf = pbuf + 2 * NT;
+    wbuf = pbuf + 4 * NT;
+    tvbuf = wbuf + (NT / 32) * 256;
+    coffbuf = reinterpret_cast<int *>(tvbuf + (NT / 32) * 32);
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
     v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
@@ -1500,13 +1565,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kBand) {
       __syncthreads();
       const T *fac = reinterpret_cast<const T *>(S.fac);
-      const int64_t rec = (int64_t)32 * (D.W + 32);
       const int nb = D.npad / 32;
       const T *F = fac + D.fac_off;
+      const T *Bw = F + (int64_t)nb * D.rec;
       if (L.nstages >= 6)
-        band_solve_chain<T, CT, NT, 6>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
+        band_solve_chain<T, CT, NT, 6>(F, Bw, nb, D.W, D.w, D.rec, slot_len, ybuf, pbuf, wbuf,
+                                       tvbuf, coffbuf, ring);
       else
-        band_solve_chain<T, CT, NT, 4>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
+        band_solve_chain<T, CT, NT, 4>(F, Bw, nb, D.W, D.w, D.rec, slot_len, ybuf, pbuf, wbuf,
+                                       tvbuf, coffbuf, ring);
     } else if (KIND == kCGS) {
       if (tid == 0) {
         const bool ok = mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);
@@ -1681,203 +1748,285 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     }
   } else {
     // ----------------------------------------------------------- ASYNC
-    // per-launch update budget starts from zero (this CTA's own subdomains)
-    if (tid == 0)
-      for (int it = i0; it < i1; ++it) {
-        const Item item = L.items[it];
-        L.sys[item.sys].sub[item.p].step_updates = 0;
-      }
-    __syncthreads();
-    uint64_t t_idle = gtimer();
-    for (;;) {
-      int any_work = 0, all_done = 1;
-      for (int it = i0; it < i1; ++it) {
-        load_item(it);
-        const int p = s_flag[5];
-        SubState &ss = s_sys.sub[p];
-        SysState *st = s_sys.st;
-        if (tid == 0) {
-          const uint32_t wd = ld_acquire_u32(&st->word);
-          int action = 0;  // 0 none, 1 update, 2 park, 3 check
-          const int phase = (int)(wd & 3u);
-          const int epoch = (int)(wd >> 2);
-          if (ld_relaxed_s32(&L.ctl->abort)) action = -1;
-          else if (phase != kDone) {
-            s_flag[3] = 0;
-            if (phase == kRun) {
-              // decentralized detection: the global flag, raised here or seen
-              // on a neighbour, stops this subdomain (it parks)
-              bool flag = false;
-              if (decentral) {
-                flag = ld_relaxed_s32(&ss.gconv_epoch) == epoch;
-                if (!flag) {
-                  const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-                  for (int q = 0; q < s_sub.n_nbr && !flag; ++q)
-                    flag = ld_acquire_s32(&s_sys.sub[nb[q]].gconv_epoch) == epoch;
-                  if (flag) st_release_s32(&ss.gconv_epoch, epoch);
-                }
+    // One visit of item `it`: decide and perform its next action (update,
+    // park, post-termination check). Returns -1 on abort, 0 when the item had
+    // nothing to do, 1 after doing something; not_done is set while the
+    // item's system has not finished.
+    auto async_item = [&](int it, int &not_done) -> int {
+      load_item(it);
+      const int p = s_flag[5];
+      SubState &ss = s_sys.sub[p];
+      SysState *st = s_sys.st;
+      if (tid == 0) {
+        const uint32_t wd = ld_acquire_u32(&st->word);
+        int action = 0;  // 0 none, 1 update, 2 park, 3 check
+        const int phase = (int)(wd & 3u);
+        const int epoch = (int)(wd >> 2);
+        if (ld_relaxed_s32(&L.ctl->abort)) action = -1;
+        else if (phase != kDone) {
+          s_flag[3] = 0;
+          if (phase == kRun) {
+            // decentralized detection: the global flag, raised here or seen
+            // on a neighbour, stops this subdomain (it parks)
+            bool flag = false;
+            if (decentral) {
+              flag = ld_relaxed_s32(&ss.gconv_epoch) == epoch;
+              if (!flag) {
+                const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+                for (int q = 0; q < s_sub.n_nbr && !flag; ++q)
+                  flag = ld_acquire_s32(&s_sys.sub[nb[q]].gconv_epoch) == epoch;
+                if (flag) st_release_s32(&ss.gconv_epoch, epoch);
               }
-              if (flag) {
-                if (ss.park_epoch != epoch) action = 2;
-              } else if (ss.updates >= L.max_updates) {
-                st->status = kENOCONV;
-                atomicCAS(&st->word, wd, ((uint32_t)epoch << 2) | kDone);
-              } else if (ss.step_updates < L.step_limit) {
-                action = 1;
-                if (L.fresh && ss.updates > 0 && s_sub.n_nbr > 0) {
-                  // wait for new neighbour data instead of repeating the solve
-                  // on the same interface values
-                  uint64_t seen = 0;
-                  const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-                  for (int q = 0; q < s_sub.n_nbr; ++q)
-                    seen += ld_relaxed_u32(&s_sys.sub[nb[q]].version);
-                  if (seen == ss.nbr_seen) action = 0;
-                }
-              }
-            } else if (phase == kDrain) {
-              if (ss.park_epoch != epoch) action = 2;
-            } else {
-              if (ss.check_epoch != epoch) action = 3;
             }
+            if (flag) {
+              if (ss.park_epoch != epoch) action = 2;
+            } else if (ss.updates >= L.max_updates) {
+              st->status = kENOCONV;
+              if (atomicCAS(&st->word, wd, ((uint32_t)epoch << 2) | kDone) == wd)
+                atomicSub(&L.ctl->remaining, 1);
+            } else if (ss.step_updates < L.step_limit) {
+              action = 1;
+              if (L.fresh && ss.updates > 0 && s_sub.n_nbr > 0) {
+                // wait for new neighbour data instead of repeating the solve
+                // on the same interface values
+                uint64_t seen = 0;
+                const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+                for (int q = 0; q < s_sub.n_nbr; ++q)
+                  seen += ld_relaxed_u32(&s_sys.sub[nb[q]].version);
+                if (seen == ss.nbr_seen) action = 0;
+              }
+            }
+          } else if (phase == kDrain) {
+            if (ss.park_epoch != epoch) action = 2;
+          } else {
+            if (ss.check_epoch != epoch) action = 3;
           }
-          s_flag[0] = action;
-          s_flag[1] = (int)wd;
-          s_flag[2] = (phase != kDone) ? 1 : 0;
+        }
+        s_flag[0] = action;
+        s_flag[1] = (int)wd;
+        s_flag[2] = (phase != kDone) ? 1 : 0;
+      }
+      __syncthreads();
+      const int action = s_flag[0];
+      const uint32_t wd = (uint32_t)s_flag[1];
+      if (action < 0) return -1;
+      if (s_flag[2]) not_done = 1;
+      if (action == 0) return 0;
+      const int epoch = (int)(wd >> 2);
+      if (action == 1) {
+        // acquire the neighbours' published versions before reading x: the
+        // lanes of warp 0 take one neighbour each, so the acquires are in
+        // flight together; the barrier then orders every thread's reads of
+        // x after them
+        if (tid < 32) {
+          uint64_t seen = 0;
+          const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+          for (int q = tid; q < s_sub.n_nbr; q += 32) {
+            const uint32_t v = ld_acquire_u32(&s_sys.sub[nb[q]].version);
+            seen += v;
+            if (q < 32) s_seq[q] = v;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(0xffffffffu, seen, o);
+          if (tid == 0) {
+            if (ss.updates > 0 && seen == ss.nbr_seen) ss.stale += 1;
+            ss.nbr_seen = seen;
+          }
         }
         __syncthreads();
-        const int action = s_flag[0];
-        const uint32_t wd = (uint32_t)s_flag[1];
-        if (action < 0) goto out;
-        if (s_flag[2]) all_done = 0;
-        if (action == 0) continue;
-        any_work = 1;
-        const int epoch = (int)(wd >> 2);
-        if (action == 1) {
-          // acquire the neighbours' published versions before reading x: the
-          // lanes of warp 0 take one neighbour each, so the acquires are in
-          // flight together; the barrier then orders every thread's reads of
-          // x after them
-          if (tid < 32) {
-            uint64_t seen = 0;
-            const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-            for (int q = tid; q < s_sub.n_nbr; q += 32) {
-              const uint32_t v = ld_acquire_u32(&s_sys.sub[nb[q]].version);
-              seen += v;
-              if (q < 32) s_seq[q] = v;
+        double rl, ro;
+        if (!update(s_sys.x, s_sys.x, rl, ro)) return -1;
+        if (tid == 0) {
+          // every thread fenced its owned-row stores before update()'s
+          // final barrier; the release store publishes them
+          ss.updates += 1;
+          ss.step_updates += 1;
+          st_release_u32(&ss.version, (uint32_t)(2 * ss.updates));
+          // local criterion (Eq. 2) on the residual gathered before the update
+          const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
+          if (decentral) {
+            // publish the local status; a converged subdomain whose
+            // neighbours all report local convergence raises the global flag
+            st_release_s32(&ss.conv_epoch, conv ? epoch : -1);
+            if (conv) {
+              bool all = true;
+              const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
+              for (int q = 0; q < s_sub.n_nbr && all; ++q)
+                all = ld_acquire_s32(&s_sys.sub[nb[q]].conv_epoch) == epoch;
+              if (all) st_release_s32(&ss.gconv_epoch, epoch);
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) seen += __shfl_xor_sync(0xffffffffu, seen, o);
-            if (tid == 0) {
-              if (ss.updates > 0 && seen == ss.nbr_seen) ss.stale += 1;
-              ss.nbr_seen = seen;
-            }
+          } else if (conv && ss.conv_epoch != epoch) {
+            ss.conv_epoch = epoch;
+            const int nc = atomicAdd(&st->nconv, 1) + 1;
+            if (nc == s_sys.P) atomicCAS(&st->word, ((uint32_t)epoch << 2) | kRun,
+                                         ((uint32_t)epoch << 2) | kDrain);
+          } else if (!conv && ss.conv_epoch == epoch) {
+            ss.conv_epoch = -1;
+            atomicSub(&st->nconv, 1);
           }
-          __syncthreads();
-          double rl, ro;
-          if (!update(s_sys.x, s_sys.x, rl, ro)) goto out;
-          if (tid == 0) {
-            // every thread fenced its owned-row stores before update()'s
-            // final barrier; the release store publishes them
-            ss.updates += 1;
-            ss.step_updates += 1;
-            st_release_u32(&ss.version, (uint32_t)(2 * ss.updates));
-            // local criterion (Eq. 2) on the residual gathered before the update
-            const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
-            if (decentral) {
-              // publish the local status; a converged subdomain whose
-              // neighbours all report local convergence raises the global flag
-              st_release_s32(&ss.conv_epoch, conv ? epoch : -1);
-              if (conv) {
-                bool all = true;
-                const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-                for (int q = 0; q < s_sub.n_nbr && all; ++q)
-                  all = ld_acquire_s32(&s_sys.sub[nb[q]].conv_epoch) == epoch;
-                if (all) st_release_s32(&ss.gconv_epoch, epoch);
-              }
-            } else if (conv && ss.conv_epoch != epoch) {
-              ss.conv_epoch = epoch;
-              const int nc = atomicAdd(&st->nconv, 1) + 1;
-              if (nc == s_sys.P) atomicCAS(&st->word, ((uint32_t)epoch << 2) | kRun,
-                                           ((uint32_t)epoch << 2) | kDrain);
-            } else if (!conv && ss.conv_epoch == epoch) {
-              ss.conv_epoch = -1;
-              atomicSub(&st->nconv, 1);
-            }
-          }
-        } else if (action == 2) {
-          if (tid == 0) {
-            ss.park_epoch = epoch;
+        }
+      } else if (action == 2) {
+        if (tid == 0) {
+          ss.park_epoch = epoch;
+          __threadfence();
+          const int np = atomicAdd(&st->nparked, 1) + 1;
+          if (np == s_sys.P) {
             __threadfence();
-            const int np = atomicAdd(&st->nparked, 1) + 1;
-            if (np == s_sys.P) {
-              __threadfence();
-              st_release_u32(&st->word, ((uint32_t)epoch << 2) | kCheck);
-            }
+            st_release_u32(&st->word, ((uint32_t)epoch << 2) | kCheck);
           }
-        } else {
-          // post-termination check: owned residual of the (now frozen) x
-          const SysDesc &S = s_sys;
-          const SubDesc &D = s_sub;
-          const int K = S.K;
-          const int64_t eb = D.row_off * K;
-          double o = 0.0, dmy = 0.0;
-          for (int i = tid; i < D.n; i += NT) {
-            if (!S.ownf[D.row_off + i]) continue;
-            double r = S.b[S.gidx[D.row_off + i]];
-            for (int k = 0; k < K; ++k) {
-              const int64_t e = eb + (int64_t)k * D.npad + i;
-              r -= S.rval[e] * ld_relaxed_f64(S.x + S.rcol[e]);
-            }
-            o += r * r;
+        }
+      } else {
+        // post-termination check: owned residual of the (now frozen) x
+        const SysDesc &S = s_sys;
+        const SubDesc &D = s_sub;
+        const int K = S.K;
+        const int64_t eb = D.row_off * K;
+        double o = 0.0, dmy = 0.0;
+        for (int i = tid; i < D.n; i += NT) {
+          if (!S.ownf[D.row_off + i]) continue;
+          double r = S.b[S.gidx[D.row_off + i]];
+          for (int k = 0; k < K; ++k) {
+            const int64_t e = eb + (int64_t)k * D.npad + i;
+            r -= S.rval[e] * ld_relaxed_f64(S.x + S.rcol[e]);
           }
-          block_sum2<NT>(o, dmy, s_red);
-          if (tid < 32) {
-            int last = 0;
+          o += r * r;
+        }
+        block_sum2<NT>(o, dmy, s_red);
+        if (tid < 32) {
+          int last = 0;
+          if (tid == 0) {
+            st_relaxed_f64(&ss.part[0], o);
+            ss.check_epoch = epoch;
+            __threadfence();
+            last = (atomicAdd(&st->nchecked, 1) + 1 == S.P) ? 1 : 0;
+            if (last) __threadfence();
+          }
+          last = __shfl_sync(0xffffffffu, last, 0);
+          if (last) {
+            const double res2 = warp_sum_partials(S.sub, S.P, 0, true);
             if (tid == 0) {
-              st_relaxed_f64(&ss.part[0], o);
-              ss.check_epoch = epoch;
-              __threadfence();
-              last = (atomicAdd(&st->nchecked, 1) + 1 == S.P) ? 1 : 0;
-              if (last) __threadfence();
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last) {
-              const double res2 = warp_sum_partials(S.sub, S.P, 0, true);
-              if (tid == 0) {
-                st->res2 = res2;
-                uint32_t nw;
-                if (res2 < S.tol2 * st->b2 || res2 == 0.0) {
-                  st->status = kOK;
-                  nw = ((uint32_t)epoch << 2) | kDone;
-                } else if (ld_relaxed_s32(&st->restarts) >= L.max_restarts) {
-                  st->status = kENOCONV;
-                  nw = ((uint32_t)epoch << 2) | kDone;
-                } else {
-                  st->restarts += 1;
-                  st->nconv = 0;
-                  st->nparked = 0;
-                  st->nchecked = 0;
-                  nw = ((uint32_t)(epoch + 1) << 2) | kRun;
-                }
-                __threadfence();
-                st_release_u32(&st->word, nw);
+              st->res2 = res2;
+              uint32_t nw;
+              if (res2 < S.tol2 * st->b2 || res2 == 0.0) {
+                st->status = kOK;
+                nw = ((uint32_t)epoch << 2) | kDone;
+              } else if (ld_relaxed_s32(&st->restarts) >= L.max_restarts) {
+                st->status = kENOCONV;
+                nw = ((uint32_t)epoch << 2) | kDone;
+              } else {
+                st->restarts += 1;
+                st->nconv = 0;
+                st->nparked = 0;
+                st->nchecked = 0;
+                nw = ((uint32_t)(epoch + 1) << 2) | kRun;
               }
+              __threadfence();
+              st_release_u32(&st->word, nw);
+              if ((nw & 3u) == (uint32_t)kDone) atomicSub(&L.ctl->remaining, 1);
             }
           }
+        }
+        __syncthreads();
+      }
+      return 1;
+    };
+    if (!dyn) {
+      // static schedule: this CTA's own subdomains, in turn. The per-launch
+      // update budget starts from zero
+      if (tid == 0)
+        for (int it = i0; it < i1; ++it) {
+          const Item item = L.items[it];
+          L.sys[item.sys].sub[item.p].step_updates = 0;
+        }
+      __syncthreads();
+      uint64_t t_idle = gtimer();
+      for (;;) {
+        int any_work = 0, all_done = 1;
+        for (int it = i0; it < i1; ++it) {
+          int not_done = 0;
+          const int r = async_item(it, not_done);
+          if (r < 0) goto out;
+          if (not_done) all_done = 0;
+          if (r > 0) any_work = 1;
+        }
+        if (all_done) break;
+        if (tid == 0 && past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
+        if (any_work) {
+          t_idle = gtimer();
+        } else {
+          if (!L.persist) break;
+          // thread 0 decides, so that every thread leaves together
+          if (tid == 0) s_dyn[0] = (int64_t)(gtimer() - t_idle) > L.timeout_ns ? 1 : 0;
           __syncthreads();
+          if (s_dyn[0]) {
+            if (tid == 0) set_error(L.ctl, kETIMEOUT, 3);
+            break;
+          }
+          __nanosleep(500);
         }
       }
-      if (all_done) break;
-      if (tid == 0 && past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
-      if (any_work) {
-        t_idle = gtimer();
-      } else {
-        if (!L.persist) break;
-        if ((int64_t)(gtimer() - t_idle) > L.timeout_ns) {
-          if (tid == 0) set_error(L.ctl, kETIMEOUT, 3);
-          break;
+    } else {
+      // dynamic schedule (one persistent launch over every SM): CTAs take
+      // tickets t = 0, 1, 2, ... from one counter and visit item t mod
+      // nitems, so every subdomain is visited once per round of tickets
+      // whichever CTA is free (equal update rates without equal subdomain
+      // counts per CTA). A per-subdomain lock taken with an acquire CAS and
+      // released with a release store gives one CTA at a time the
+      // subdomain's state; a ticket whose subdomain is busy is skipped.
+      // CTAs stop when every system of the launch has finished.
+      uint64_t t_idle = gtimer();  // thread 0's: last time a ticket found work
+      int misses = 0;              // thread 0's: tickets without work since then
+      for (;;) {
+        __syncthreads();  // every thread has read the previous ticket
+        if (tid == 0) {
+          int it = -1, stop = 0;
+          if (ld_relaxed_s32(&L.ctl->abort)) {
+            stop = 1;
+          } else if (ld_acquire_s32(&L.ctl->remaining) <= 0) {
+            stop = 2;
+          } else if (misses >= L.nitems) {
+            // a whole round of tickets found nothing to do: back off, and
+            // give up once the idle limit has passed
+            misses = 0;
+            if ((int64_t)(gtimer() - t_idle) > L.timeout_ns) {
+              set_error(L.ctl, kETIMEOUT, 3);
+              stop = 3;
+            } else {
+              __nanosleep(500);
+            }
+          }
+          if (!stop) {
+            const unsigned long long t = atomicAdd(&L.ctl->ticket, 1ull);
+            it = (int)(t % (unsigned long long)L.nitems);
+            const Item item = L.items[it];
+            if (atom_cas_acquire_u32(&L.sys[item.sys].sub[item.p].busy, 0u, 1u) != 0u) it = -1;
+          }
+          s_dyn[0] = stop;
+          s_dyn[1] = it;
         }
-        __nanosleep(500);
+        __syncthreads();
+        const int stop = s_dyn[0], it = s_dyn[1];
+        if (stop) break;
+        int r = 0;
+        if (it >= 0) {
+          int not_done = 0;
+          r = async_item(it, not_done);
+          if (tid == 0) {
+            const Item item = L.items[it];
+            __threadfence();
+            st_release_u32(&L.sys[item.sys].sub[item.p].busy, 0u);
+          }
+          if (r < 0) goto out;
+        }
+        if (tid == 0) {
+          if (r > 0) {
+            t_idle = gtimer();
+            misses = 0;
+          } else {
+            ++misses;
+          }
+          if (past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
+        }
       }
     }
   }

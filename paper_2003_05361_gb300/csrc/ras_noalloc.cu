@@ -87,19 +87,28 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) *out = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
 }
 
-// Device address of g_relres_scratch for each device, looked up once per
-// device with that device current (the host-side name of the array is only a
-// stand-in and must never be passed to a kernel).
+// Device address of g_relres_scratch for each device, looked up with that
+// device current (the host-side name of the array is only a stand-in and
+// must never be passed to a kernel). The first call on a device does the
+// look-up; later calls that are not being captured into a CUDA graph look it
+// up again (a cheap table query once the module is loaded), so the address
+// stays right even after cudaDeviceReset reloads the module; calls made
+// during a capture use the address cached by an earlier call.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch_addr[kMaxDevices] = {};
 
-ras_status scratch_for_current_device(double **out) {
+ras_status scratch_for_current_device(cudaStream_t st, double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RAS_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return RAS_ENOTSUP;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();  // the query itself is not an error of this call
+    cs = cudaStreamCaptureStatusActive;  // treat an unanswerable query as a capture
+  }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || cs == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_relres_scratch) != cudaSuccess || !p) return RAS_ECUDA;
     g_scratch_addr[dev] = static_cast<double *>(p);
@@ -115,11 +124,11 @@ extern "C" ras_status ras_relres_noalloc(int32_t n, const int32_t *row_ptr, cons
                                          double *relres, void *cuda_stream) {
   if (n <= 0 || !row_ptr || !col_idx || !val || !b || !x || !relres) return RAS_EINVAL;
   if ((int64_t)n > (int64_t)kChunkRows * kMaxChunks) return RAS_EINVAL;  // beyond the scratch
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double *scratch = nullptr;
-  ras_status s = scratch_for_current_device(&scratch);
+  ras_status s = scratch_for_current_device(st, &scratch);
   if (s != RAS_OK) return s;
   const int nchunks = (n + kChunkRows - 1) / kChunkRows;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   relres_partials_kernel<<<nchunks, kThreads, 0, st>>>(n, row_ptr, col_idx, val, b, x, scratch);
   relres_final_kernel<<<1, kThreads, 0, st>>>(nchunks, scratch, relres);
   return cudaGetLastError() == cudaSuccess ? RAS_OK : RAS_ECUDA;

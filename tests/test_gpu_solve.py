@@ -379,3 +379,32 @@ def test_host_buffers_entry_point():
     assert abs(ras.ras_relres(ctx, torch.tensor(b, device="cuda"), torch.tensor(x, device="cuda"))
                - true_relres(A, b, x)) < 1e-12
     ras.ras_destroy(ctx)
+
+
+@pytest.mark.parametrize("dynamic", ["1", "0"])
+@pytest.mark.parametrize("kind,prec", [(BAND, F32), (CG, F32)])
+def test_async_schedules_converge(dynamic, kind, prec, monkeypatch):
+    # asynchronous solves take subdomains by ticket on every co-resident CTA
+    # slot (the default) or keep the static assignment (RAS_ASYNC_DYNAMIC=0):
+    # both reach the tolerance and the oracle's direct solution, and with
+    # tickets every subdomain is updated at about the same rate
+    monkeypatch.setenv("RAS_ASYNC_DYNAMIC", dynamic)
+    N = 256
+    A = problems.poisson2d(N)
+    b = problems.rhs_uniform(A.n, 9)
+    part = ras.ras_partition_regular2d(N, N, 8, 8)
+    ctx = ras.ras_setup(A, part, 64, 4, kind, prec, 10)
+    static_grid = ras.ras_get_launch(ctx)["grid"]
+    xs = oracle.poisson2d_direct(N, b)
+    for rep in range(2):
+        x, info = gpu_solve(A, b, part, 64, 4, kind, prec, 10, mode=ras.RAS_ASYNC, tol=1e-10,
+                            ctx=ctx)
+        assert info.status == 0, info.as_dict()
+        assert true_relres(A, b, x) < 1e-10
+        assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+        if dynamic == "1":
+            assert static_grid <= info.grid <= 64
+            assert info.updates_max <= 1.5 * info.updates_min + 2
+        else:
+            assert info.grid == static_grid
+    ras.ras_destroy(ctx)
