@@ -436,7 +436,7 @@ def run_ours(args):
         # every section is reported, never fatal to the headline line
         for name, fn in (("band_config4", lambda: band_config4(dev, stream, args.band_iters)),
                          ("config3", lambda: config3_section(dev, stream)),
-                         ("config4", lambda: config4_section(dev, stream)),
+                         ("config4", lambda: config4_section(dev, stream, args.config4_full)),
                          ("serving", lambda: serving_section(args)),
                          ("nonsymmetric", lambda: nonsymmetric(dev, stream)),
                          ("oras", lambda: oras_section(dev, stream))):
@@ -582,18 +582,21 @@ def config3_section(dev, stream):
     return out
 
 
-def config4_section(dev, stream):
+def config4_section(dev, stream, full: bool = False, cap: int = 200):
     """Config 4: 2D diffusion 2048^2 (4,194,304 unknowns), k = exp(GRF sigma 1,
     ell 1/32, seed 4), b uniform seed 4, regular 32x32 = 1024 subdomains,
     overlap 4, banded Cholesky factorised in FP64 and stored in FP32, BF16 or
-    FP64: time to 1e-8, synchronous for every storage precision and
-    asynchronous with FP32 factors (one solve each, L2 flushed). A direct
-    solve of the full system is out of the oracle's reach (a 69 GB band), so
-    the full-size results are compared with each other and their FP64
-    residuals reported; the error against the oracle's FP64 direct solve is
-    taken on the same recipe at 256^2 with the same 64 x 64 subdomains and
+    FP64. Time to 1e-8 (one solve each, L2 flushed) for FP32 factors,
+    synchronous and asynchronous; BF16 and FP64 factors, which take the same
+    number of synchronous iterations (the outer iteration is FP64), are timed
+    over `cap` synchronous iterations and their time to 1e-8 estimated as
+    time per iteration x the FP32 count (full=True solves them to 1e-8 too).
+    A direct solve of the full system is out of the oracle's reach (a 69 GB
+    band), so the full-size results are compared with each other and their
+    FP64 residuals reported; the error against the oracle's FP64 direct solve
+    is taken on the same recipe at 256^2 with the same 64 x 64 subdomains and
     overlap (4 x 4 parts), where the oracle's banded Cholesky of the whole
-    system is feasible."""
+    system is feasible, for every storage precision."""
     import torch
 
     import paper_2003_05361_gb300 as ras
@@ -615,7 +618,9 @@ def config4_section(dev, stream):
             modes = (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)) if name == "fp32" else \
                 (("sync", ras.RAS_SYNC),)
             for mname, mode in modes:
-                info, x = _timed_solve(ras, ctx, bd, A.n, dev, TOL, mode, flush)
+                capped = n == 2048 and name != "fp32" and not full
+                info, x = _timed_solve(ras, ctx, bd, A.n, dev, TOL, mode, flush,
+                                       cap if capped else 0)
                 row = _info_row(info)
                 if n == 2048:
                     counts = ras.ras_get_update_counts(ctx)
@@ -624,16 +629,25 @@ def config4_section(dev, stream):
                     ach = alg / (info.kernel_ms / 1e3) / 1e9
                     row["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak,
                                        "unit": "GB/s", "frac": ach / peak,
-                                       "peak_source": peak_src, "algorithmic_bytes": alg}
+                                       "peak_source": peak_src, "algorithmic_bytes": alg,
+                                       "kernel": f"ras_main_kernel<band, {name}, "
+                                                 f"{ras.ras_get_launch(ctx)['cta_threads']}>"}
+                    row["ms_per_iteration"] = info.kernel_ms / max(info.updates_median, 1)
+                    if capped:
+                        row["capped_at"] = cap
+                        it32 = rows["sync_fp32"]["iterations"]
+                        row["estimated_ms_to_tol"] = row["ms_per_iteration"] * it32
+                if not (n == 2048 and capped):
+                    xsol[f"{mname}_{name}"] = x.cpu().numpy()
                 rows[f"{mname}_{name}"] = row
-                xsol[f"{mname}_{name}"] = x.cpu().numpy()
             ras.ras_destroy(ctx)
         if n == 2048:
             out.update(rows)
-            ref = xsol["sync_fp64"]
+            ref = xsol.get("sync_fp64", xsol["sync_fp32"])
             nr = float(np.linalg.norm(ref))
-            out["difference_vs_fp64_factors"] = {
-                k: float(np.linalg.norm(v - ref)) / nr for k, v in xsol.items() if k != "sync_fp64"}
+            out["difference_between_results"] = {
+                "reference": "sync_fp64" if "sync_fp64" in xsol else "sync_fp32",
+                **{k: float(np.linalg.norm(v - ref)) / nr for k, v in xsol.items()}}
         else:
             import oracle
 
@@ -982,6 +996,38 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve_sweep(args):
+    """Serving at several loads: the sync-FP64 saturation throughput is
+    measured first (every request of a burst present at t = 0), then async
+    mixed precision (FP32 factors) and sync FP64 each serve an open-loop
+    Poisson stream at 0.5, 0.8 and 0.95 x that throughput (the rates of the
+    serving reading), --serve-requests requests per point."""
+    import torch
+
+    import paper_2003_05361_gb300 as ras
+    from paper_2003_05361_gb300.serve import Server, request_stream
+
+    torch.cuda.set_device(0)
+    sat = Server(mode=ras.RAS_SYNC, prec=ras.RAS_FP64, step_limit=args.serve_step,
+                 workers=args.serve_workers).run(request_stream(args.serve_sat_requests, rate=1e6,
+                                                                seed=7))
+    mu = sat["solves_per_s"]
+    print(json.dumps({"saturation_sync_fp64": sat}), flush=True)
+    rows = []
+    for frac in (0.5, 0.8, 0.95):
+        for name, mode, prec in (("async_fp32", ras.RAS_ASYNC, ras.RAS_FP32),
+                                 ("sync_fp64", ras.RAS_SYNC, ras.RAS_FP64)):
+            srv = Server(mode=mode, prec=prec, step_limit=args.serve_step,
+                         workers=args.serve_workers)
+            st = srv.run(request_stream(args.serve_requests, rate=frac * mu, seed=5))
+            row = {"load": frac, "rate_per_s": frac * mu, "arm": name, **st}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"serve_sweep": f"{args.serve_requests} requests per point, side U{{64..512}}, "
+                                     f"sync-FP64 saturation {mu:.3f} solves/s", "rows": rows}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1000,6 +1046,8 @@ def main():
     ap.add_argument("--sweep-reps", type=int, default=10,
                     help="asynchronous solves per sweep point (median, min, max)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload only")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving at 0.5 / 0.8 / 0.95 x the sync-FP64 saturation throughput")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-step", type=int, default=20)
@@ -1008,12 +1056,16 @@ def main():
                     help="requests of the saturation run in the default benchmark")
     ap.add_argument("--serve-requests-bench", type=int, default=60,
                     help="requests per serving arm in the default benchmark")
-    ap.add_argument("--sections", default="band_config4,config3,config4,serving,nonsymmetric,oras",
+    ap.add_argument("--config4-full", action="store_true",
+                    help="solve config 4 to 1e-8 with every storage precision")
+    ap.add_argument("--sections", default="config3,config4,serving,nonsymmetric,oras",
                     help="comma-separated extra sections of the default run")
     args = ap.parse_args()
     args.sections = [x for x in args.sections.split(",") if x]
     if args.sweep:
         run_sweep(args)
+    elif args.serve_sweep:
+        run_serve_sweep(args)
     elif args.serve:
         run_serving(args)
     elif args.profile:

@@ -52,7 +52,8 @@ class ras_solve_info(C.Structure):
 
 class ras_tune_result(C.Structure):
     _fields_ = [("cta_threads", C.c_int32), ("staged", C.c_int32), ("inner_iters", C.c_int32),
-                ("candidates", C.c_int32), ("score", C.c_double)]
+                ("candidates", C.c_int32), ("score", C.c_double), ("schedule", C.c_int32),
+                ("grid", C.c_int32), ("per_cta", C.c_int32), ("reserved_", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -188,6 +188,10 @@ struct ras_ctx {
   int maxw = 0;  // largest true local half-bandwidth
   int exec_kind = 0;  // kernel variant (LocalKind; kCGS for staged FP32 CG)
   int nt_pref = 0;    // preferred CTA threads of the CG / ILU variants (0: default)
+  int sched = -1;     // asynchronous schedule: -1 RAS_ASYNC_DYNAMIC (default dynamic),
+                      // 0 static assignment, 1 dynamic (tickets)
+  int grid_cap = 0;   // cap on the CTAs of a launch (0: every co-resident slot); with the
+                      // static assignment it sets the subdomains per CTA
   // host copies of the maps (inspection)
   std::vector<std::vector<int32_t>> omega, iface;
   std::vector<std::vector<uint8_t>> owned;
@@ -203,7 +207,7 @@ struct ras_ctx {
   uint32_t *d_cpair = nullptr;
   int32_t *d_own_g = nullptr;
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
-          *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr;
+          *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr, *d_tnbr = nullptr;
   uint8_t *d_ownf = nullptr;
   double *d_rval = nullptr, *d_xalt = nullptr, *d_xg = nullptr;
   void *d_fac = nullptr, *d_lval = nullptr;
@@ -493,7 +497,7 @@ void assign_items(LaunchPlan &pl, const std::vector<Item> &items, const std::vec
 
 ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Item> &items,
                        const std::vector<double> &cost, int Wmax, int npad_max, int kmax,
-                       cudaStream_t stream, int nt_pref = 0) {
+                       cudaStream_t stream, int nt_pref = 0, int grid_cap = 0) {
   pl.release();
   int dev = 0, nsm = 0, max_smem = 0;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -530,6 +534,7 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   int64_t cap = (int64_t)occ * nsm;
   const int64_t lim = env_int("RAS_MAX_CTAS", 0);
   if (lim > 0) cap = std::min<int64_t>(cap, lim);
+  if (grid_cap > 0) cap = std::min<int64_t>(cap, grid_cap);
   // as many CTAs as give every CTA the same number of subdomains (the most
   // any CTA would get anyway): a synchronous iteration takes as long as its
   // fullest CTA either way, and in the asynchronous mode subdomains then
@@ -592,6 +597,7 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.lev_ptr = c->d_levp;
   s.lev_rows = c->d_levr;
   s.nbr = c->d_nbr;
+  s.tnbr = c->d_tnbr;
   s.kry = c->d_kry;
   s.kry_ld = c->kry_ld;
   return s;
@@ -778,8 +784,6 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     d.npad = (d.n + 31) / 32 * 32;
     d.n_own = (int32_t)owned_lists[p].size();
     d.W = (std::max(mp.w, 1) + 3) / 4 * 4;  // band records: W a multiple of 4
-    d.w = mp.w;
-    d.rec = banded ? band_rec_entries(mp.w, d.W, 16 / (int)prec_bytes(prec)) : 0;
     d.row_off = rows;
     d.own_off = owns;
     d.fac_off = fac;
@@ -790,7 +794,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     nbrs += d.n_nbr;
     if (banded) {
       if (mp.w > (kind == RAS_LOCAL_BANDLU ? kMaxBandLuW : kMaxBandW)) return RAS_ENOTSUP;
-      fac += 2ll * (d.npad / 32) * d.rec;  // forward and backward compact records
+      fac += 2ll * (d.npad / 32) * 32 * (d.W + 32);  // forward and backward records
       Wmax = std::max(Wmax, d.W);
       c->cost[p] = (double)d.npad * (d.W + 1) * 2.0 + 12.0 * d.n * K;
     } else {
@@ -975,6 +979,38 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   CUDA_TRY(cudaEventCreate(&c->evk0));
   CUDA_TRY(cudaEventCreate(&c->evk1));
   CUDA_TRY(cudaEventCreateWithFlags(&c->ev_begin, cudaEventDisableTiming));
+  // spanning tree of the subdomain graph (breadth-first from subdomain 0, a
+  // new root for every further component): the decentralized convergence
+  // detection elects its leader along these edges
+  std::vector<int32_t> tnbr;
+  {
+    std::vector<std::vector<int32_t>> tadj(P);
+    std::vector<char> seen(P, 0);
+    std::vector<int32_t> queue;
+    queue.reserve(P);
+    for (int r = 0; r < P; ++r) {
+      if (seen[r]) continue;
+      seen[r] = 1;
+      queue.assign(1, r);
+      for (size_t h = 0; h < queue.size(); ++h) {
+        const int p = queue[h];
+        for (int32_t q : maps[p].nbr) {
+          if (seen[q]) continue;
+          seen[q] = 1;
+          tadj[p].push_back(q);
+          tadj[q].push_back(p);
+          queue.push_back(q);
+        }
+      }
+    }
+    for (int p = 0; p < P; ++p) {
+      std::sort(tadj[p].begin(), tadj[p].end());
+      c->subs[p].tnbr_off = (int32_t)tnbr.size();
+      c->subs[p].n_tnbr = (int32_t)tadj[p].size();
+      tnbr.insert(tnbr.end(), tadj[p].begin(), tadj[p].end());
+    }
+  }
+  if ((st = c->upload(c->d_tnbr, tnbr)) != RAS_OK) return st;
   if ((st = c->upload(c->d_subs, c->subs)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_sub, P)) != RAS_OK) return st;
   if ((st = c->alloc(c->d_st, 1)) != RAS_OK) return st;
@@ -1023,7 +1059,6 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         lj.W = d.W;
         lj.K = Kb;
         lj.nb = d.npad / 32;
-        lj.rec = d.rec;
         lj.band_off = band_off[p];
         lj.fac_off = d.fac_off;
         ljobs.push_back(lj);
@@ -1192,6 +1227,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     c->exec_kind = kind;
     st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax, npad_max, K, c->stream);
   }
+  c->sched = -1;
+  c->grid_cap = 0;
   if (st != RAS_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->last_updates.assign(P, 0);
@@ -1205,7 +1242,7 @@ namespace {
 ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &pl,
                      SysDesc *d_sys, int nsys, GridCtl *d_ctl, GridCtl *h_ctl, int32_t mode,
                      int64_t max_updates, int m, cudaEvent_t ev0, cudaEvent_t ev1,
-                     cudaEvent_t evk0, cudaEvent_t evk1, int *grid_out) {
+                     cudaEvent_t evk0, cudaEvent_t evk1, int *grid_out, int sched = -1) {
   Launch L{};
   L.sys = d_sys;
   L.nsys = nsys;
@@ -1232,8 +1269,10 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.nstages = pl.nstages;
   const int nitems = (int)pl.items.size();
   L.nitems = nitems;
-  // asynchronous solves run on the dynamic schedule unless RAS_ASYNC_DYNAMIC=0
-  L.dynamic = (mode != RAS_SYNC && env_int("RAS_ASYNC_DYNAMIC", 1) != 0) ? 1 : 0;
+  // asynchronous solves run on the dynamic schedule unless the context chose
+  // the static assignment (ras_autotune) or RAS_ASYNC_DYNAMIC=0
+  const int dyn = sched >= 0 ? sched : (env_int("RAS_ASYNC_DYNAMIC", 1) != 0 ? 1 : 0);
+  L.dynamic = (mode != RAS_SYNC && dyn) ? 1 : 0;
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   CUDA_TRY(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
@@ -1297,7 +1336,7 @@ ras_status ras_solve(ras_ctx *c, const double *b, double *x, double tol, int32_t
   int grid = 0;
   ras_status rs = run_solve(c->stream, c->exec_kind, c->ls.prec, c->plan, c->d_sysdesc, 1, c->d_ctl,
                             c->h_ctl, mode, max_updates, c->ls.inner_iters, c->ev0, c->ev1,
-                            c->evk0, c->evk1, &grid);
+                            c->evk0, c->evk1, &grid, c->sched);
   if (rs != RAS_OK) return rs;
   CUDA_TRY(cudaMemcpyAsync(c->h_st, c->d_st, sizeof(SysState), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(GridCtl), cudaMemcpyDeviceToHost, c->stream));
@@ -1635,8 +1674,12 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
   }
   double *b = c->d_bx;
   CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * c->n, c->stream));
+  // candidates: kernel variant and CTA threads, inner steps, and the launch
+  // shape: asynchronous schedule (tickets on every slot, or the static
+  // assignment) and a cap on the CTAs (every co-resident slot, or half of the
+  // subdomains: two subdomains per CTA at least, fewer CTAs per SM)
   struct Cand {
-    int exec_kind, nt, m;
+    int exec_kind, nt, m, sched, grid_cap;
   };
   std::vector<Cand> cands;
   const int kind = c->ls.kind, prec = c->ls.prec, m0 = c->ls.inner_iters;
@@ -1647,34 +1690,39 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
     // GMRES: the Krylov scratch holds at most the set-up step count
     if (kind != RAS_LOCAL_GMRES) ms.push_back(2 * m0);
   }
+  const bool async = mode != RAS_SYNC;
+  std::vector<std::pair<int, int>> shapes = {{1, 0}, {0, 0}, {0, (c->P + 1) / 2}};
+  if (!async) shapes = {{0, 0}, {0, (c->P + 1) / 2}};
   for (int m : ms) {
+    std::vector<std::pair<int, int>> variants;  // (exec_kind, threads)
     if (banded) {
-      cands.push_back({kBand, 128, m});
-      cands.push_back({kBand, 256, m});
+      variants = {{kBand, 128}, {kBand, 256}};
     } else {
       const int ek = kind == RAS_LOCAL_GMRES ? kGMRES : kind;
-      cands.push_back({ek, 256, m});
-      cands.push_back({ek, 512, m});
-      if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && c->d_lcol16) cands.push_back({kCGS, 512, m});
+      variants = {{ek, 256}, {ek, 512}};
+      if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && c->d_lcol16) variants.push_back({kCGS, 512});
     }
+    for (auto &v : variants)
+      for (auto &sh : shapes) cands.push_back({v.first, v.second, m, sh.first, sh.second});
   }
   std::vector<Item> items(c->P);
   for (int p = 0; p < c->P; ++p) items[p] = {0, p, 0, 0};
-  const Cand saved = {c->exec_kind, c->nt_pref, m0};
+  const Cand saved = {c->exec_kind, c->nt_pref, m0, c->sched, c->grid_cap};
   double best = -1.0;
   Cand pick = saved;
-  int tried = 0;
+  int tried = 0, pick_grid = 0;
   for (const Cand &cd : cands) {
     LaunchPlan pl;
     if (plan_launch(pl, cd.exec_kind, prec, items, c->cost, c->plan.Wmax, c->plan.npad_max, c->K,
-                    c->stream, cd.nt) != RAS_OK) {
+                    c->stream, cd.nt, cd.grid_cap) != RAS_OK) {
       pl.release();
       continue;
     }
     std::swap(pl, c->plan);
-    const int ek = c->exec_kind;
+    const int ek = c->exec_kind, sk = c->sched;
     c->exec_kind = cd.exec_kind;
     c->ls.inner_iters = cd.m;
+    c->sched = cd.sched;
     // window 1 (transient), then window 2 from its result (timed): the score
     // is the residual reduction per kernel millisecond of window 2
     CUDA_TRY(launch_fill(x_scratch, 1.0, c->n, c->stream));
@@ -1683,6 +1731,7 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
     if (rs == RAS_OK || rs == RAS_ENOCONV) rs = ras_solve(c, b, x_scratch, 1e-300, mode, iters, &info);
     std::swap(pl, c->plan);
     c->exec_kind = ek;
+    c->sched = sk;
     pl.release();
     if (rs != RAS_OK && rs != RAS_ENOCONV) continue;
     ++tried;
@@ -1691,22 +1740,31 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
     if (score > best) {
       best = score;
       pick = cd;
+      pick_grid = info.grid;
     }
   }
   c->ls.inner_iters = pick.m;
   c->exec_kind = pick.exec_kind;
   c->nt_pref = pick.nt;
-  if (pick.exec_kind != saved.exec_kind || pick.nt != saved.nt) {
+  c->sched = async ? pick.sched : saved.sched;
+  c->grid_cap = pick.grid_cap;
+  if (pick.exec_kind != saved.exec_kind || pick.nt != saved.nt || pick.grid_cap != saved.grid_cap) {
     ras_status st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax,
-                                c->plan.npad_max, c->K, c->stream, c->nt_pref);
+                                c->plan.npad_max, c->K, c->stream, c->nt_pref, c->grid_cap);
     if (st != RAS_OK) return st;
   }
   if (out) {
+    std::memset(out, 0, sizeof(*out));
     out->cta_threads = c->plan.nt;
     out->staged = c->exec_kind == kCGS ? 1 : 0;
     out->inner_iters = c->ls.inner_iters;
     out->candidates = tried;
     out->score = best;
+    out->schedule = async ? pick.sched : 0;
+    out->grid = pick_grid;
+    out->per_cta = (async && pick.sched == 1)
+                       ? 0
+                       : (int32_t)((c->P + c->plan.grid - 1) / std::max(c->plan.grid, 1));
   }
   return tried > 0 ? RAS_OK : RAS_ENOTSUP;
 }

@@ -36,92 +36,23 @@ enum : int32_t { kRun = 0, kDrain = 1, kCheck = 2, kDone = 3 };
 #define RAS_HD
 #endif
 
-// Compact band records (banded Cholesky / LU solves). Rows are grouped in
-// blocks of 32; the record of block K holds, column by column (column-major,
-// lane = row), only the rows [lo, lo + len) of each column that can be
-// non-zero, rounded out to whole 16-byte chunks of G = 16 / sizeof(value)
-// rows. With w the true local half-bandwidth and W >= w the window width (a
-// multiple of 4), the columns of the forward record of block K are
-//   c in [0, 32):   column c of L_KK^{-1} (lower triangle: rows >= c);
-//   c in [32, 64):  column c-32 of M_K = L_KK^{-1} L[K rows, block K-1] (dense,
-//                   or empty where the band does not reach: c-32 < 32-w);
-//   c in [64, 32+W): the rows of L of block K+1 in the columns of its window
-//                   left of block K, L[32K+32+l][32K+32-W+k], k = c-64
-//                   (rows l <= k - (W-w));
-// and of the backward record of block K (U = L^T for Cholesky, U for LU):
-//   c in [0, 32):   column c of U_KK^{-1} (upper triangle: rows <= c);
-//   c in [32, 64):  column c-32 of M'_K = U_KK^{-1} U[K rows, block K+1] (dense,
-//                   or empty for c-32 > w-1);
-//   c in [64, 32+W): the rows of U of block K-1 in the columns of its window
-//                   right of block K, U[32K-32+l][32K+32+k], k = c-64
-//                   (rows l >= k + 64 - w).
-// The chained solve then needs, per block, the band's own non-zeros (plus the
-// 32 x 32 near-block product) and no dense 32 x (32 + W) operator.
-struct BandCol {
-  int32_t lo, len;
-};
-RAS_HD inline BandCol band_col(int c, int dir, int w, int W, int G) {
-  BandCol r{0, 0};
-  if (c < 32) {
-    if (dir == 0) {
-      r.lo = c / G * G;
-      r.len = 32 - r.lo;
-    } else {
-      const int hi = (c + G) / G * G;  // rows [0, c] rounded up
-      r.len = hi < 32 ? hi : 32;
-    }
-  } else if (c < 64) {
-    // near-block product: column c-32 is zero when the band cannot reach it
-    // (forward: row 32K-32+(c-32) is more than w left of row 32K+31)
-    const int k = c - 32;
-    if (dir == 0 ? k >= 32 - w : k <= w - 1) r.len = 32;
-  } else {
-    const int k = c - 64;
-    if (dir == 0) {
-      const int u = k - (W - w) + 1;  // rows [0, u)
-      if (u > 0) {
-        const int hi = (u + G - 1) / G * G;
-        r.len = hi < 32 ? hi : 32;
-      }
-    } else {
-      const int lo = k + 64 - w;  // rows [lo, 32)
-      if (lo < 32) {
-        r.lo = (lo > 0 ? lo : 0) / G * G;
-        r.len = 32 - r.lo;
-      }
-    }
-  }
-  return r;
-}
-RAS_HD inline int band_ncol(int W) { return 64 + (W > 32 ? W - 32 : 0); }
-// Entries of one record (the same for both directions; the larger is taken).
-RAS_HD inline int band_rec_entries(int w, int W, int G) {
-  int f = 0, b = 0;
-  const int nc = band_ncol(W);
-  for (int c = 0; c < nc; ++c) {
-    f += band_col(c, 0, w, W, G).len;
-    b += band_col(c, 1, w, W, G).len;
-  }
-  return f > b ? f : b;
-}
-
 struct SubDesc {
   int32_t n;        // |Omega_p|
   int32_t npad;     // n rounded up to a multiple of 32
   int32_t n_own;    // |O_p|
   int32_t W;        // band: half-bandwidth w rounded up to a multiple of 4 (>= 4)
-  int32_t w;        // band: true local half-bandwidth
-  int32_t rec;      // band: entries of one compact record (see band_col)
   int64_t row_off;  // offset of local row 0 in the per-row arrays (multiple of 32)
   int64_t own_off;  // offset into own_l
-  int64_t fac_off;  // band: nb forward records, then nb backward records (rec entries
-                    // each; forward from L, backward from U = L^T (Cholesky) or U (LU))
+  int64_t fac_off;  // band: nb forward records, then nb backward records (32 x (W+32) each)
+                    // (forward from L, backward from U = L^T (Cholesky) or U (LU))
   int64_t lev_off;  // ILU: offset into lev_ptr (forward levels, then backward)
   int64_t lrow_off; // ILU: offset into lev_rows (n forward rows, then n backward)
   int32_t nlev_f;   // ILU: number of forward / backward levels
   int32_t nlev_b;
   int32_t nbr_off;  // neighbour subdomains (system-local ids) in nbr[]
   int32_t n_nbr;
+  int32_t tnbr_off;  // neighbours in a spanning tree of the subdomain graph (tnbr[])
+  int32_t n_tnbr;
 };
 
 struct SubState {
@@ -142,6 +73,8 @@ struct SubState {
   int32_t check_epoch;
   int32_t gconv_epoch;  // decentralized detection: epoch of the global flag (-1: none)
   uint32_t busy;        // async, dynamic schedule: 1 while a CTA holds the subdomain
+  unsigned long long report;  // decentralized detection: (epoch << 32) | tree neighbour
+                              // the convergence report was sent to (epoch -1: none)
 };
 
 struct SysState {
@@ -202,6 +135,7 @@ struct SysDesc {
   const int32_t *lev_ptr;
   const int32_t *lev_rows;
   const int32_t *nbr;
+  const int32_t *tnbr;  // spanning-tree neighbours (decentralized detection)
   // GMRES: Krylov basis scratch in the local-solve precision, kry_ld vectors
   // of npad entries per subdomain from row_off * kry_ld (vector q of local
   // row i at row_off * kry_ld + q * npad + i); kry_ld - 1 bounds the steps

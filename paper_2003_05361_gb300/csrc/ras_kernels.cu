@@ -74,6 +74,19 @@ __device__ __forceinline__ uint32_t atom_cas_acquire_u32(uint32_t *p, uint32_t c
                : "memory");
   return old;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ int ld_acquire_s32(const int *p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -425,25 +438,22 @@ __global__ void __launch_bounds__(256) band_lu_kernel(const BandJob *jobs, doubl
 // --------------------------------------------------------------------------
 //
 // Rows are grouped in blocks of 32 (K = 0..nb-1; rows >= n are identity rows).
-// With L_KK the diagonal block of the lower factor, forward substitution block
-// by block is
-//   y_K = L_KK^{-1} (r_K - L[K rows, block K-1] y_{K-1} - L[K rows, older] y_older)
-//       = L_KK^{-1} t_K - M_K y_{K-1},
-//   t_K = r_K - L[K rows, older] y_older,  M_K = L_KK^{-1} L[K rows, block K-1],
-// where "older" are the window rows [32K - W, 32K - 32) left of block K-1, and
-// backward substitution with the upper factor U mirrors it:
-//   z_K = U_KK^{-1} t'_K - M'_K z_{K+1},  t'_K = y_K - U[K rows, older] z_older,
-//   M'_K = U_KK^{-1} U[K rows, block K+1].
+// With L_KK the diagonal block of the lower factor and W = the local
+// half-bandwidth w, forward substitution block by block is
+//   y_K = L_KK^{-1} (r_K - L_{K,left} y_left) = t_K - M_K y[32K-W, 32K),
+//   t_K = L_KK^{-1} r_K,  M_K = L_KK^{-1} L[K rows, 32K-W .. 32K)   (32 x W)
+// and backward substitution with the upper factor U
+//   z_K = t'_K - M'_K z[32K+32, 32K+32+W),  t'_K = U_KK^{-1} y_K,
+//   M'_K = U_KK^{-1} U[K rows, 32K+32 .. 32K+32+W)                   (32 x W).
 // Cholesky: L from the band (ld = w+1), U = L^T, so U_KK^{-1} = (L_KK^{-1})^T.
 // LU: unit lower L and U from one band (ld = 2w+1), U_KK inverted on its own.
-// The record of block K holds [inverse diagonal block | M | the older-window
-// rows of the NEXT block of the pass] in the compact column layout of
-// band_col (ras_internal.h): a chain step applies the inverse to t_K and M_K
-// to the previous block, both before one CTA barrier, and accumulates the
-// next block's older-window sum t alongside, so the step still has one
-// barrier while the bytes read are those of the band itself (plus the 32 x 32
-// near-block product). Per subdomain: nb forward records, then nb backward
-// records, jb.rec entries each.
+// Per subdomain the storage is nb forward records, then nb backward records,
+// each a column-major 32 x (32 + W) matrix (entry (l, j) at j*32 + l):
+//   forward  record K = [ L_KK^{-1} | M_K  ],
+//   backward record K = [ U_KK^{-1} | M'_K ],
+// so that a chain step reads one contiguous record and every one of its
+// 32 + W columns is applied to one broadcast value (the step's own right-hand
+// side for the first 32, a finished window row for the rest).
 template <typename T, bool LU>
 __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
                                                          const double *band, T *fac) {
@@ -517,54 +527,35 @@ __global__ void __launch_bounds__(32) band_layout_kernel(const LayoutJob *jobs,
     for (int r = 0; r < 32; ++r) Y[LU ? r : 0][m] = col[r];
     __syncwarp();
   }
-  // compact records (band_col): forward record K of block K, backward record K
-  constexpr int G = 16 / (int)sizeof(T);
-  const int64_t rec = jb.rec;
+  const int64_t rec = (int64_t)32 * (W + 32);
   T *F = fac + jb.fac_off + (int64_t)K * rec;
   T *Bk = fac + jb.fac_off + (int64_t)nb * rec + (int64_t)K * rec;
-  // entries of the factors, zero outside the band and the matrix
-  auto Lv = [&](int r, int c) -> double {  // lower factor (strictly below the diagonal here)
-    return (r < n && c >= 0 && c < r && r - c <= w) ? at(r, c) : 0.0;
-  };
-  auto Uv = [&](int r, int c) -> double {  // upper factor (strictly right of the diagonal here)
-    if (r < 0 || r >= n || c >= n || c <= r || c - r > w) return 0.0;
-    return LU ? at(r, c) : at(c, r);  // Cholesky: U = L^T
-  };
-  const int ncol = band_ncol(W);
-  int64_t off = 0;
-  for (int c = 0; c < ncol; ++c) {
-    const BandCol bc = band_col(c, 0, w, W, G);
-    if (bc.len == 0) continue;
-    double v;
-    if (c < 32) {
-      v = X[l][c];  // L_KK^{-1}, zero above the diagonal
-    } else if (c < 64) {
-      const int col = 32 * K - 32 + (c - 32);  // near block K-1
-      v = 0.0;
-      for (int m = 0; m <= l; ++m) v += X[l][m] * Lv(32 * K + m, col);
-    } else {
-      v = Lv(32 * K + 32 + l, 32 * K + 32 - W + (c - 64));  // block K+1, left of block K
-    }
-    if (l >= bc.lo && l < bc.lo + bc.len) F[off + (l - bc.lo)] = from_double<T>(v);
-    off += bc.len;
+  for (int m = 0; m < 32; ++m) {
+    F[m * 32 + l] = from_double<T>(X[l][m]);                           // L_KK^{-1}[l][m]
+    Bk[m * 32 + l] = from_double<T>(LU ? Y[LU ? l : 0][m] : X[m][l]);  // U_KK^{-1}[l][m]
   }
-  off = 0;
-  for (int c = 0; c < ncol; ++c) {
-    const BandCol bc = band_col(c, 1, w, W, G);
-    if (bc.len == 0) continue;
-    double v;
-    if (c < 32) {
-      v = LU ? Y[LU ? l : 0][c] : X[c][l];  // U_KK^{-1}, zero below the diagonal
-    } else if (c < 64) {
-      const int col = 32 * K + 32 + (c - 32);  // near block K+1
-      v = 0.0;
-      for (int m = l; m < 32; ++m)
-        v += (LU ? Y[LU ? l : 0][m] : X[m][l]) * Uv(32 * K + m, col);
-    } else {
-      v = Uv(32 * K - 32 + l, 32 * K + 32 + (c - 64));  // block K-1, right of block K
-    }
-    if (l >= bc.lo && l < bc.lo + bc.len) Bk[off + (l - bc.lo)] = from_double<T>(v);
-    off += bc.len;
+  // M_K[l][c] = sum_{m <= l} Linv[l][m] L[32K+m][32K-W+c]
+  for (int c = 0; c < W; ++c) {
+    const int col = 32 * K - W + c;
+    double s = 0.0;
+    if (col >= 0)
+      for (int m = 0; m <= l; ++m) {
+        const int r = 32 * K + m;
+        if (r < n && col >= r - w) s += X[l][m] * at(r, col);
+      }
+    F[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
+  }
+  // M'_K[l][c] = sum_{m >= l} Uinv[l][m] U[32K+m][32K+32+c]
+  // (Cholesky: U[a][b] = L[b][a])
+  for (int c = 0; c < W; ++c) {
+    const int r = 32 * K + 32 + c;
+    double s = 0.0;
+    if (r < n)
+      for (int m = l; m < 32; ++m) {
+        const int col = 32 * K + m;
+        if (col >= r - w) s += LU ? Y[LU ? l : 0][m] * at(col, r) : X[m][l] * at(r, col);
+      }
+    Bk[(int64_t)(32 + c) * 32 + l] = from_double<T>(s);
   }
 }
 
@@ -601,6 +592,7 @@ __global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
     s.check_epoch = -1;
     s.gconv_epoch = -1;
     s.busy = 0;
+    s.report = 0xffffffff00000000ull;  // epoch -1: no report
   }
 }
 
@@ -683,95 +675,70 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
-// Entries of one warp's ring slot in the band chain: an even share of the
-// largest compact record for window Wmax (w = Wmax) plus one straddling
-// column, in whole 16-byte chunks (G values).
-__host__ __device__ inline int band_slot_len(int Wmax, int NW, int G) {
-  const int per = (band_rec_entries(Wmax, Wmax, G) + NW - 1) / NW + 32 + G;
-  return (per + G - 1) / G * G;
+// Columns of a band record each warp of an NW-warp CTA takes per chain step:
+// ceil((W + 32) / NW) rounded up to a multiple of 4 (W itself is a multiple of
+// 4), so every warp's first column, and the broadcast values it reads, are
+// 16-byte aligned.
+__host__ __device__ inline int band_cols_per_warp(int W, int NW) {
+  return ((W + 32 + NW - 1) / NW + 3) / 4 * 4;
 }
 
-// Banded Cholesky (or LU) solve L U delta = r by the whole CTA as two block
-// chains over the compact records of band_col (forward with L, backward with
-// U). Step K of the forward pass computes
-//   y_K = L_KK^{-1} t_K - M_K y_{K-1}            (one CTA barrier)
-//   t_{K+1} = r_{K+1} - L[block K+1, older window] y_older
-// where t_K was formed at step K-1; the backward pass mirrors it with U and
-// z. Each warp takes a contiguous run of the record's columns, balanced by
-// stored entries (the run [coff[q0], coff[q1]) is contiguous in memory), and
-// accumulates two partial sums per row: the new block (inverse and near-block
-// columns, applied to the warp's copy of t and to the previous block) and the
-// next block's older-window sum. After the barrier every warp adds the
-// partials of all warps in the same fixed order, so all warps hold identical
-// y_K and t_{K+1}. Copies: each warp streams its own run of record s + D - 1
-// into a private D-slot ring with 16-byte cp.async while it computes step s;
-// a copy is waited for by the thread that issued it (cp.async.wait_group) and
-// published to the warp by __syncwarp, and a slot is refilled one step after
-// it was read. Each warp keeps the last 8 finished blocks in its own ring win
-// (row g at g & 255; rows outside [0, npad) read slots not yet written, which
-// hold zero). y[0..npad) holds r on entry and delta on exit; part holds 4 NT
-// partials, tv 32 values per warp, coff ncol + 1 ints.
+// Banded Cholesky solve L L^T delta = r by the whole CTA as two block chains:
+// forward y_K = L_KK^{-1} r_K - M_K y_window, backward
+// z_K = U_KK^{-1} y_K - M'_K z_window. A chain step applies the 32 + W columns
+// of one record (see band_layout_kernel) to broadcast values: column j < 32 to
+// row 32K + j of the step's own input (r in the forward pass, y in the
+// backward pass, read from y before the step overwrites it), window column
+// j = 32 + c to finished row 32K - W + c (forward) or 32K + 32 + c (backward).
+// Warp w takes the contiguous columns [w tw, (w+1) tw) (band_cols_per_warp)
+// and writes its 32 partial sums; after ONE barrier every warp adds the
+// partials in the same fixed order, so all warps hold identical y_K. Window
+// sums enter with a minus sign.
+// Each warp streams its own columns of record s + D - 1 with 16-byte cp.async
+// copies into a private D-slot ring while it computes step s; a copy is waited
+// for by the thread that issued it and published to the warp by __syncwarp,
+// so the chain needs no mbarrier and no second barrier. A slot is refilled one
+// step after it was read, behind that step's barrier. Each warp keeps its own
+// copy of the last 8 finished blocks in win (row g at g & 255, stored twice,
+// at +0 and +256, so that a warp's window rows are one unwrapped run); window
+// rows outside [0, npad) meet zero operator columns and read zero-initialised
+// slots. y[0..npad) holds r on entry and delta on exit; part holds 2 NT
+// partials.
 template <typename T, typename CT, int NT, int D>
 __device__ void band_solve_chain(const T *__restrict__ F, const T *__restrict__ Bs, int nb, int W,
-                                 int w, int rec, int slot_len, CT *y, CT *part, CT *win, CT *tv,
-                                 int *coff, T *ring) {
+                                 int twm, CT *y, CT *part, CT *win, T *ring) {
   constexpr int NW = NT / 32;
-  constexpr int G = 16 / (int)sizeof(T);  // values per 16-byte copy
+  constexpr int V = 16 / (int)sizeof(T);  // values per 16-byte copy
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ncol = band_ncol(W);
+  const int NI = W + 32;
+  const int tw = band_cols_per_warp(W, NW);
+  const int j0 = warp * tw < NI ? warp * tw : NI;
+  const int j1 = j0 + tw < NI ? j0 + tw : NI;
+  const int cnt = j1 - j0;
+  const int nd = (j1 < 32 ? j1 : 32) - (j0 < 32 ? j0 : 32);  // own-input columns
+  const int nchunk = cnt * 32 / V;  // 16-byte chunks of this warp's columns
+  const int64_t rec = (int64_t)32 * NI;
+  const int slot_len = twm * 32;
   T *rw = ring + (size_t)warp * D * slot_len;
-  CT *wy = win + warp * 256;
-  CT *wt = tv + warp * 32;
+  CT *wy = win + warp * 512;  // two copies of an 8-block ring: reads never wrap
   for (int dir = 0; dir < 2; ++dir) {
-    // column offsets of this direction's records: exclusive prefix sums of
-    // the column lengths (warp 0)
-    __syncthreads();  // the previous pass is done with coff
-    if (warp == 0) {
-      int run = 0;
-      for (int c0 = 0; c0 < ncol; c0 += 32) {
-        const int c = c0 + lane;
-        const int len = c < ncol ? band_col(c, dir, w, W, G).len : 0;
-        int v = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int u = __shfl_up_sync(0xffffffffu, v, o);
-          if (lane >= o) v += u;
-        }
-        if (c < ncol) coff[c] = run + v - len;
-        run += __shfl_sync(0xffffffffu, v, 31);
-      }
-      if (lane == 0) coff[ncol] = run;
-    }
-    __syncthreads();
-    const int total = coff[ncol];
-    // this warp's columns [q0, q1): the first column at or past its share
-    auto first_at = [&](int target) -> int {
-      for (int c0 = 0; c0 < ncol; c0 += 32) {
-        const int c = c0 + lane;
-        const unsigned m = __ballot_sync(0xffffffffu, c < ncol && coff[c] >= target);
-        if (m) return c0 + __ffs(m) - 1;
-      }
-      return ncol;
-    };
-    const int q0 = warp == 0 ? 0 : first_at((int)((int64_t)total * warp / NW));
-    const int q1 = warp == NW - 1 ? ncol : first_at((int)((int64_t)total * (warp + 1) / NW));
-    const int e0 = coff[q0];
-    const int nchunk = (coff[q1] - e0) / G;
-    const T *src_l = (dir == 0 ? F : Bs) + e0;
+    const T *src_l = (dir == 0 ? F : Bs) + (int64_t)j0 * 32 + lane * V;
+    T *dst_l = rw + lane * V;
     // copies of chain step s into ring slot sl (one commit group, maybe empty)
     auto issue = [&](int s, int sl) {
       if (s < nb) {
-        const T *src = src_l + (int64_t)(dir == 0 ? s : nb - 1 - s) * rec;
-        T *dst = rw + sl * slot_len;
-        for (int q = lane; q < nchunk; q += 32) cp_async16(dst + q * G, src + q * G);
+        const T *src = src_l + (dir == 0 ? s : nb - 1 - s) * rec;
+        T *dst = dst_l + sl * slot_len;
+        for (int q0 = 0; q0 < nchunk; q0 += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (q0 + u * 32 + lane < nchunk) cp_async16(dst + (q0 + u * 32) * V, src + (q0 + u * 32) * V);
+        }
       }
       cp_async_commit();
     };
 #pragma unroll
-    for (int q = 0; q < 8; ++q) wy[q * 32 + lane] = CT(0);
-    // t of the first block of the pass (its older window lies outside the
-    // subdomain): r_0 forward, y_{nb-1} backward
-    wt[lane] = y[32 * (dir == 0 ? 0 : nb - 1) + lane];
+    for (int q = 0; q < 16; ++q) wy[q * 32 + lane] = CT(0);
 #pragma unroll
     for (int s = 0; s < D - 1; ++s) issue(s, s);
     int cur = 0;  // slot of step s
@@ -781,39 +748,41 @@ __device__ void band_solve_chain(const T *__restrict__ F, const T *__restrict__ 
       __syncwarp();
       const int K = dir == 0 ? s : nb - 1 - s;
       const T *sl = rw + cur * slot_len + lane;
-      // rows of the near block: forward 32K - 32 + k, backward 32K + 32 + k;
-      // of the next block's older window: forward 32K + 32 - W + k, backward
-      // 32K + 32 + k
-      const int nbase = dir == 0 ? 32 * K - 64 : 32 * K;
-      const int obase = dir == 0 ? 32 * K + 32 - W - 64 : 32 * K + 32 - 64;
-      CT a0 = CT(0), a1 = CT(0), ao = CT(0);
-      int off = 0;
-      for (int c = q0; c < q1; ++c) {
-        const BandCol bc = band_col(c, dir, w, W, G);
-        if (bc.len == 0) continue;
-        const int r = lane - bc.lo;
-        const CT v = (r >= 0 && r < bc.len) ? to_ct(sl[off - bc.lo]) : CT(0);
-        off += bc.len;
-        if (c < 32) a0 += v * wt[c];
-        else if (c < 64) a1 -= v * wy[(nbase + c) & 255];
-        else ao -= v * wy[(obase + c) & 255];
-      }
-      CT *pb = part + (s & 1) * 2 * NT;
-      pb[warp * 32 + lane] = a0 + a1;
-      pb[NT + warp * 32 + lane] = ao;
-      __syncthreads();
-      // every warp forms the same y_K and t of the next block
-      CT v = CT(0), o = CT(0);
+      CT a[4] = {CT(0), CT(0), CT(0), CT(0)};
+      int ii = 0;
+      if (nd > 0) {
+        const CT *ys = y + 32 * K + j0;  // own input rows 32K + j
+        for (; ii < nd; ii += 4) {
+          CT bv[4];
+          ld4(ys + ii, bv);
 #pragma unroll
-      for (int q = 0; q < NW; ++q) {
-        v += pb[q * 32 + lane];
-        o += pb[NT + q * 32 + lane];
+          for (int u = 0; u < 4; ++u)
+            if (ii + u < nd) a[u] += to_ct(sl[(ii + u) * 32]) * bv[u];
+        }
+        ii = nd;
       }
+      if (ii < cnt) {
+        // window row of column j: 32K - W - 32 + j (forward), 32K + j (backward)
+        const int g0 = (dir == 0 ? 32 * K - W - 32 : 32 * K) + j0;
+        const CT *ws = wy + (g0 & 255);
+        for (; ii < cnt; ii += 4) {
+          CT bv[4];
+          ld4(ws + ii, bv);
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (ii + u < cnt) a[u] -= to_ct(sl[(ii + u) * 32]) * bv[u];
+        }
+      }
+      CT *pb = part + (s & 1) * NT;
+      pb[warp * 32 + lane] = (a[0] + a[1]) + (a[2] + a[3]);
+      __syncthreads();
+      // every warp forms the same y_K
+      CT v = CT(0);
+#pragma unroll
+      for (int w = 0; w < NW; ++w) v += pb[w * 32 + lane];
       wy[(K & 7) * 32 + lane] = v;
+      wy[256 + (K & 7) * 32 + lane] = v;
       if (warp == 0) y[32 * K + lane] = v;
-      const int Kn = dir == 0 ? K + 1 : K - 1;
-      if (Kn >= 0 && Kn < nb) wt[lane] = y[32 * Kn + lane] + o;
-      __syncwarp();
       cur = cur + 1 == D ? 0 : cur + 1;
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -1394,23 +1363,19 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
 template <int KIND, typename T, int NT>
 struct Smem {
   using CT = typename CTypeOf<T>::type;
-  // band: copy rings | y | partials | window rings | t | column offsets ;
-  // cg: r p q d ; ilu: r z p q d ;
+  // band: copy rings | y | partials | window rings ; cg: r p q d ; ilu: r z p q d ;
   // staged cg: A_p values | A_p columns | p ; gmres: r w v d | GmresSmem
-  static constexpr int G = 16 / (int)sizeof(T);
-  static __host__ __device__ int band_slot(int Wmax) { return band_slot_len(Wmax, NT / 32, G); }
+  static __host__ __device__ int band_twm(int Wmax) { return band_cols_per_warp(Wmax, NT / 32); }
   static __host__ __device__ size_t ylen(int Wmax, int npad_max) {
     return ((size_t)npad_max + 31) / 32 * 32;
   }
   static __host__ __device__ size_t vec_len(int npad_max) { return ((size_t)npad_max + 31) / 32 * 32; }
   static __host__ __device__ size_t bytes(int Wmax, int npad_max, int kmax, int nstages) {
     if (KIND == kBand) {
-      size_t b = (size_t)(NT / 32) * nstages * band_slot(Wmax) * sizeof(T);  // copy rings
+      size_t b = (size_t)(NT / 32) * nstages * band_twm(Wmax) * 32 * sizeof(T);  // copy rings
       b += ylen(Wmax, npad_max) * sizeof(CT);     // y (r / delta)
-      b += 4 * NT * sizeof(CT);                   // partials: two buffers x two sums
-      b += (size_t)(NT / 32) * 256 * sizeof(CT);  // per-warp window rings
-      b += (size_t)(NT / 32) * 32 * sizeof(CT);   // per-warp t
-      b += ((size_t)band_ncol(Wmax) + 1 + 3) / 4 * 4 * sizeof(int);  // column offsets
+      b += 2 * NT * sizeof(CT);                   // partials, two buffers
+      b += (size_t)(NT / 32) * 512 * sizeof(CT);  // per-warp window rings (two copies)
       return b;
     }
     if (KIND == kCGS) {
@@ -1457,16 +1422,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   // shared-memory carve-up
   T *ring = nullptr;
   CT *ybuf = nullptr, *pbuf = nullptr, *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *v3 = nullptr,
-     *v4 = nullptr, *wbuf = nullptr, *tvbuf = nullptr, *gsm = nullptr;
-  int *coffbuf = nullptr;
-  const int slot_len = KIND == kBand ? SM::band_slot(L.Wmax) : 0;
+     *v4 = nullptr, *wbuf = nullptr, *gsm = nullptr;
+  const int twm = SM::band_twm(L.Wmax);
   if (KIND == kBand) {
     ring = reinterpret_cast<T *>(smem);
-    ybuf = reinterpret_cast<CT *>(smem + (size_t)(NT / 32) * L.nstages * slot_len * sizeof(T));
+    ybuf = reinterpret_cast<CT *>(smem + (size_t)(NT / 32) * L.nstages * twm * 32 * sizeof(T));
     pbuf = ybuf + SM::ylen(L.Wmax, L.npad_max);
-    wbuf = pbuf + 4 * NT;
-    tvbuf = wbuf + (NT / 32) * 256;
-    coffbuf = reinterpret_cast<int *>(tvbuf + (NT / 32) * 32);
+    wbuf = pbuf + 2 * NT;
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
     v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
@@ -1565,15 +1527,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kBand) {
       __syncthreads();
       const T *fac = reinterpret_cast<const T *>(S.fac);
+      const int64_t rec = (int64_t)32 * (D.W + 32);
       const int nb = D.npad / 32;
       const T *F = fac + D.fac_off;
-      const T *Bw = F + (int64_t)nb * D.rec;
       if (L.nstages >= 6)
-        band_solve_chain<T, CT, NT, 6>(F, Bw, nb, D.W, D.w, D.rec, slot_len, ybuf, pbuf, wbuf,
-                                       tvbuf, coffbuf, ring);
+        band_solve_chain<T, CT, NT, 6>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
       else
-        band_solve_chain<T, CT, NT, 4>(F, Bw, nb, D.W, D.w, D.rec, slot_len, ybuf, pbuf, wbuf,
-                                       tvbuf, coffbuf, ring);
+        band_solve_chain<T, CT, NT, 4>(F, F + nb * rec, nb, D.W, twm, ybuf, pbuf, wbuf, ring);
     } else if (KIND == kCGS) {
       if (tid == 0) {
         const bool ok = mbar_wait(&s_mbar[0], gcount & 1u, L.timeout_ns);
@@ -1845,15 +1805,34 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
           // local criterion (Eq. 2) on the residual gathered before the update
           const bool conv = rl < s_sys.tol2 * ss.bloc2 || rl == 0.0;
           if (decentral) {
-            // publish the local status; a converged subdomain whose
-            // neighbours all report local convergence raises the global flag
-            st_release_s32(&ss.conv_epoch, conv ? epoch : -1);
+            // leader election on a spanning tree of the subdomain graph: a
+            // locally converged subdomain that has received the convergence
+            // report of all its tree neighbours but one sends its own report
+            // to that one; one that has received all of them is a leader and
+            // raises the global flag, which then floods to every subdomain.
+            // A subdomain that loses local convergence withdraws the report
+            // it sent. Reports are tagged with the epoch, so a restart voids
+            // them.
+            const int32_t *tn = s_sys.tnbr + s_sub.tnbr_off;
+            const int nt = s_sub.n_tnbr;
+            const int p = s_flag[5];
+            int got = 0, missing = -1;
+            for (int q = 0; q < nt; ++q) {
+              const unsigned long long r = ld_acquire_u64(&s_sys.sub[tn[q]].report);
+              if ((int)(r >> 32) == epoch && (int)(uint32_t)r == p) ++got;
+              else missing = tn[q];
+            }
+            const unsigned long long mine = ld_relaxed_u64(&ss.report);
+            const bool sent = (int)(mine >> 32) == epoch;
             if (conv) {
-              bool all = true;
-              const int32_t *nb = s_sys.nbr + s_sub.nbr_off;
-              for (int q = 0; q < s_sub.n_nbr && all; ++q)
-                all = ld_acquire_s32(&s_sys.sub[nb[q]].conv_epoch) == epoch;
-              if (all) st_release_s32(&ss.gconv_epoch, epoch);
+              if (got == nt) {
+                st_release_s32(&ss.gconv_epoch, epoch);
+              } else if (got == nt - 1 && !sent) {
+                st_release_u64(&ss.report,
+                               ((unsigned long long)(uint32_t)epoch << 32) | (uint32_t)missing);
+              }
+            } else if (sent) {
+              st_release_u64(&ss.report, 0xffffffff00000000ull);
             }
           } else if (conv && ss.conv_epoch != epoch) {
             ss.conv_epoch = epoch;

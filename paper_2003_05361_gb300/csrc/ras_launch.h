@@ -18,7 +18,7 @@ struct BandJob {
 
 // One 32-row block of one subdomain for the record layout.
 struct LayoutJob {
-  int32_t n, w, W, K, nb, rec;  // rec: entries of one compact record
+  int32_t n, w, W, K, nb, pad_;
   int64_t band_off;  // FP64 band of the subdomain
   int64_t fac_off;   // first record of the subdomain (entries)
 };

@@ -254,20 +254,34 @@ def test_async_consistent_gathers_converge(kind, prec, monkeypatch):
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= 1e-6
 
 
+@pytest.mark.parametrize("mode", [ras.RAS_SYNC, ras.RAS_ASYNC])
 @pytest.mark.parametrize("kind,prec", [(CG, F32), (ILU, F32), (BAND, F32)])
-def test_autotune_then_solve(kind, prec):
+def test_autotune_then_solve(kind, prec, mode):
+    # the autotuner picks CTA threads, inner steps and the launch shape
+    # (asynchronous schedule, CTA cap = subdomains per CTA); the tuned context
+    # must still solve to the tolerance and reach the direct solution
     N = 192
     A = problems.poisson2d(N)
     b = problems.rhs_uniform(A.n, 4)
     part = ras.ras_partition_regular2d(N, N, 3, 3)
     ctx = ras.ras_setup(A, part, 9, 2, kind, prec, 10)
     xs = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-    r = ras.ras_autotune(ctx, xs, ras.RAS_SYNC, 30, True)
-    assert r.candidates >= 1 and r.cta_threads in (128, 256, 512) and r.inner_iters >= 1
+    r = ras.ras_autotune(ctx, xs, mode, 30, True)
+    assert r.candidates >= 4 and r.cta_threads in (128, 256, 512) and r.inner_iters >= 1
+    assert 1 <= r.grid <= 9 and r.schedule in (0, 1)
+    if mode == ras.RAS_SYNC:
+        assert r.schedule == 0
+    if r.schedule == 0:
+        assert r.per_cta >= 1 and r.per_cta * r.grid >= 9
+    else:
+        assert r.per_cta == 0
     launch = ras.ras_get_launch(ctx)
     assert launch["cta_threads"] == r.cta_threads and launch["inner_iters"] == r.inner_iters
-    x, info = gpu_solve(A, b, part, 9, 2, kind, prec, 10, ctx=ctx)
-    assert info.status == 0 and true_relres(A, b, x) < 1e-8
+    x, info = gpu_solve(A, b, part, 9, 2, kind, prec, 10, mode=mode, tol=1e-9, ctx=ctx)
+    assert info.status == 0 and true_relres(A, b, x) < 1e-9
+    assert info.grid == r.grid
+    xd = oracle.poisson2d_direct(N, b)
+    assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
     ras.ras_destroy(ctx)
 
 
