@@ -560,7 +560,8 @@ def config3_section(dev, stream):
                        "FP64 outer, tol 1e-8, autotuned launch",
            "setup_ms": setup_ms, "autotune_ms": tune_ms,
            "autotune": {"cta_threads": tune.cta_threads, "inner_iters": tune.inner_iters,
-                        "candidates": tune.candidates}, "launch": launch}
+                        "candidates": tune.candidates, "schedule": tune.schedule,
+                        "grid": tune.grid, "per_cta": tune.per_cta}, "launch": launch}
     peak, peak_src = measured_peaks()
     xsol = {}
     for mname, mode in (("sync", ras.RAS_SYNC), ("async", ras.RAS_ASYNC)):

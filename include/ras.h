@@ -131,9 +131,9 @@ typedef struct {
   int32_t error_site;     /* RAS_ETIMEOUT only: 1 grid barrier, 3 async idle wait,
                              4 whole-solve time limit, 5 staged-matrix copy (2 is not
                              used: the band copies complete by construction) */
-  int32_t grid;           /* CTAs of the solve's persistent launch (asynchronous
-                             solves take subdomains by ticket on every co-resident
-                             CTA slot; synchronous ones use the static plan) */
+  int32_t grid;           /* CTAs of the solve's persistent launch (on the dynamic
+                             schedule every co-resident CTA slot takes subdomains by
+                             ticket; the static plan gives each CTA a fixed set) */
 } ras_solve_info;
 
 /* ------------------------------------------------------------------------ */
@@ -199,8 +199,8 @@ typedef struct {
   int32_t inner_iters;  /* CG / PCG steps per local solve */
   int32_t candidates;   /* configurations timed */
   double score;         /* best -ln(relres) per kernel millisecond */
-  int32_t schedule;     /* asynchronous modes: 1 dynamic (CTAs take subdomains by
-                           ticket), 0 static assignment; synchronous: 0 */
+  int32_t schedule;     /* 1 dynamic (CTAs take subdomains by ticket; synchronous
+                           solves per iteration), 0 static assignment */
   int32_t grid;         /* CTAs of the tuned launch */
   int32_t per_cta;      /* static assignment: subdomains per CTA (dynamic: 0) */
   int32_t reserved_;
@@ -209,10 +209,10 @@ typedef struct {
 /* Launch-shape autotuner (not in the paper: the GPU counterpart of choosing
  * the local solver's parameters). For each candidate - CTA threads (128 / 256
  * for the banded solvers, 256 / 512 for CG and ILU-PCG, the shared-memory
- * staged FP32 CG), the launch shape (asynchronous modes: the dynamic ticket
- * schedule on every co-resident CTA slot, or the static assignment; a CTA
- * cap of every slot or half the subdomains, i.e. at least two subdomains per
- * CTA), and with tune_inner != 0 the inner step counts m/2, m, 2m - it runs the context's
+ * staged FP32 CG), the launch shape (the dynamic ticket schedule on every
+ * co-resident CTA slot, or the static assignment; a CTA cap of every slot or
+ * half the subdomains, i.e. at least two subdomains per CTA), and with
+ * tune_inner != 0 the inner step counts m/2, m, 2m - it runs the context's
  * system with a zero right-hand side from x = 1 (x_scratch: DEVICE double[n],
  * overwritten), `iters` updates and then `iters` more. With b = 0 the error is
  * x itself, dominated by the smoothest modes, so the second window's residual

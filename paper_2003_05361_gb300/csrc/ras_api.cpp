@@ -188,8 +188,8 @@ struct ras_ctx {
   int maxw = 0;  // largest true local half-bandwidth
   int exec_kind = 0;  // kernel variant (LocalKind; kCGS for staged FP32 CG)
   int nt_pref = 0;    // preferred CTA threads of the CG / ILU variants (0: default)
-  int sched = -1;     // asynchronous schedule: -1 RAS_ASYNC_DYNAMIC (default dynamic),
-                      // 0 static assignment, 1 dynamic (tickets)
+  int sched = -1;     // schedule: -1 RAS_ASYNC_DYNAMIC / RAS_SYNC_DYNAMIC (default
+                      // dynamic), 0 static assignment, 1 dynamic (tickets)
   int grid_cap = 0;   // cap on the CTAs of a launch (0: every co-resident slot); with the
                       // static assignment it sets the subdomains per CTA
   // host copies of the maps (inspection)
@@ -1269,10 +1269,14 @@ ras_status run_solve(cudaStream_t stream, int kind, int prec, const LaunchPlan &
   L.nstages = pl.nstages;
   const int nitems = (int)pl.items.size();
   L.nitems = nitems;
-  // asynchronous solves run on the dynamic schedule unless the context chose
-  // the static assignment (ras_autotune) or RAS_ASYNC_DYNAMIC=0
-  const int dyn = sched >= 0 ? sched : (env_int("RAS_ASYNC_DYNAMIC", 1) != 0 ? 1 : 0);
-  L.dynamic = (mode != RAS_SYNC && dyn) ? 1 : 0;
+  // solves run on the dynamic schedule unless the context chose the static
+  // assignment (ras_autotune) or RAS_ASYNC_DYNAMIC=0 / RAS_SYNC_DYNAMIC=0;
+  // synchronous launches take it when every CTA can hold the decision state
+  // of every system
+  const int dyn = sched >= 0 ? sched
+                             : (env_int(mode == RAS_SYNC ? "RAS_SYNC_DYNAMIC" : "RAS_ASYNC_DYNAMIC",
+                                        1) != 0 ? 1 : 0);
+  L.dynamic = (dyn && (mode != RAS_SYNC || nsys <= kMaxCtaSys)) ? 1 : 0;
   std::memset(h_ctl, 0, sizeof(GridCtl));
   h_ctl->remaining = nsys;
   CUDA_TRY(cudaMemcpyAsync(d_ctl, h_ctl, sizeof(GridCtl), cudaMemcpyHostToDevice, stream));
@@ -1691,8 +1695,7 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
     if (kind != RAS_LOCAL_GMRES) ms.push_back(2 * m0);
   }
   const bool async = mode != RAS_SYNC;
-  std::vector<std::pair<int, int>> shapes = {{1, 0}, {0, 0}, {0, (c->P + 1) / 2}};
-  if (!async) shapes = {{0, 0}, {0, (c->P + 1) / 2}};
+  const std::vector<std::pair<int, int>> shapes = {{1, 0}, {0, 0}, {0, (c->P + 1) / 2}};
   for (int m : ms) {
     std::vector<std::pair<int, int>> variants;  // (exec_kind, threads)
     if (banded) {
@@ -1746,7 +1749,7 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
   c->ls.inner_iters = pick.m;
   c->exec_kind = pick.exec_kind;
   c->nt_pref = pick.nt;
-  c->sched = async ? pick.sched : saved.sched;
+  c->sched = pick.sched;
   c->grid_cap = pick.grid_cap;
   if (pick.exec_kind != saved.exec_kind || pick.nt != saved.nt || pick.grid_cap != saved.grid_cap) {
     ras_status st = plan_launch(c->plan, c->exec_kind, prec, items, c->cost, c->plan.Wmax,
@@ -1760,9 +1763,9 @@ ras_status ras_autotune(ras_ctx *c, double *x_scratch, int32_t mode, int32_t ite
     out->inner_iters = c->ls.inner_iters;
     out->candidates = tried;
     out->score = best;
-    out->schedule = async ? pick.sched : 0;
+    out->schedule = pick.sched;
     out->grid = pick_grid;
-    out->per_cta = (async && pick.sched == 1)
+    out->per_cta = pick.sched == 1
                        ? 0
                        : (int32_t)((c->P + c->plan.grid - 1) / std::max(c->plan.grid, 1));
   }

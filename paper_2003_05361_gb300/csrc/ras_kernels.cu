@@ -215,6 +215,7 @@ __device__ bool grid_barrier(GridCtl *c, int fin, int64_t timeout_ns, int *s_fla
     const unsigned int arrived = atomicAdd(&c->count, 1u);
     if (arrived == gridDim.x - 1) {
       c->count = 0;
+      c->ticket = 0;  // next synchronous iteration of the dynamic schedule
       const int f = atomicExch(&c->fin_accum, 0);
       if (f) atomicSub(&c->remaining, f);
       __threadfence();
@@ -1413,11 +1414,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   const int tid = threadIdx.x;
   const int c = blockIdx.x;
   // static schedule: this CTA's items [i0, i1) and systems [cs0, cs1); the
-  // dynamic schedule (more CTAs than the static plan) uses neither
+  // dynamic schedules (more CTAs than the static plan) use neither
   const bool dyn = L.dynamic != 0;
   const int i0 = dyn ? 0 : L.cta_off[c], i1 = dyn ? 0 : L.cta_off[c + 1];
   const int cs0 = dyn ? 0 : L.cta_sys_off[c], cs1 = dyn ? 0 : L.cta_sys_off[c + 1];
-  const int nls = cs1 - cs0;
+  const int nls = dyn ? L.nsys : cs1 - cs0;  // systems this CTA decides for (sync)
 
   // shared-memory carve-up
   T *ring = nullptr;
@@ -1451,7 +1452,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   }
   if (tid == 0) s_flag[7] = -1;  // no system descriptor loaded yet
   for (int k = tid; k < nls; k += NT) {
-    const int sys = L.cta_sys[2 * (cs0 + k)];
+    const int sys = dyn ? k : L.cta_sys[2 * (cs0 + k)];
     s_done[k] = L.sys[sys].st->done;  // systems finished in an earlier launch stay finished
     s_iter0[k] = L.sys[sys].st->iters;
   }
@@ -1621,10 +1622,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     __threadfence();
     __syncthreads();
     if (tid == 0) {
+      // atomics: on the dynamic schedules a subdomain's updates run on
+      // different CTAs
       SubState &ph = S.sub[s_flag[5]];
-      ph.t_gather += t1 - t0;
-      ph.t_solve += t2 - t1;
-      ph.t_update += gtimer() - t2;
+      atomicAdd(reinterpret_cast<unsigned long long *>(&ph.t_gather), t1 - t0);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&ph.t_solve), t2 - t1);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&ph.t_update), gtimer() - t2);
     }
     return true;
   };
@@ -1648,9 +1651,27 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     // ------------------------------------------------------------ SYNC
     int fin = 0;
     for (int64_t j = 0; j < L.step_limit; ++j) {
-      for (int it = i0; it < i1; ++it) {
+      // one synchronous iteration: the static schedule runs this CTA's items;
+      // the dynamic one takes items by ticket until the iteration's items are
+      // gone (the counter is reset by the last CTA at the grid barrier), so
+      // uneven subdomains and item counts that do not divide by the CTAs
+      // still keep every CTA busy; either way every item is updated once
+      // from x^j, so the iterates are the same bits
+      for (int k = i0;; ++k) {
+        int it = k;
+        if (dyn) {
+          if (tid == 0) {
+            const unsigned long long t = atomicAdd(&L.ctl->ticket, 1ull);
+            s_dyn[1] = t < (unsigned long long)L.nitems ? (int)t : -1;
+          }
+          __syncthreads();
+          it = s_dyn[1];
+          if (it < 0) break;
+        } else if (k >= i1) {
+          break;
+        }
         load_item(it);
-        if (s_done[s_flag[6]]) continue;
+        if (s_done[dyn ? s_flag[7] : s_flag[6]]) continue;
         const int p = s_flag[5];
         double *xc = (j & 1) ? s_sys.xalt : s_sys.x;
         double *xn = (j & 1) ? s_sys.x : s_sys.xalt;
@@ -1659,7 +1680,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
         if (tid == 0) {
           SubState &ss = s_sys.sub[p];
           ss.part[j & 1] = ro;
-          ss.updates += 1;
+          atomicAdd(reinterpret_cast<unsigned long long *>(&ss.updates), 1ull);
         }
       }
       if (tid == 0 && past_deadline()) set_error(L.ctl, kETIMEOUT, 4);
@@ -1669,8 +1690,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       // decisions for iteration j (residual of x^j)
       for (int k = 0; k < nls; ++k) {
         if (s_done[k]) continue;
-        const int sys = L.cta_sys[2 * (cs0 + k)];
-        const int lead = L.cta_sys[2 * (cs0 + k) + 1];
+        // every CTA takes the same decision from the same bits; one (the
+        // lead) writes the system's state
+        const int sys = dyn ? k : L.cta_sys[2 * (cs0 + k)];
+        const int lead = dyn ? (blockIdx.x == 0 ? 1 : 0) : L.cta_sys[2 * (cs0 + k) + 1];
         if (tid < 32) {
           const SysDesc &S = L.sys[sys];
           const double res2 = warp_sum_partials(S.sub, S.P, (int)(j & 1), true);
