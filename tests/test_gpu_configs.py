@@ -98,3 +98,34 @@ def test_config4_full_size():
     # what two residuals below 1e-8 allow; report-level check
     d = np.linalg.norm(sols[ras.RAS_FP32] - sols[ras.RAS_BF16_STORE]) / np.linalg.norm(sols[ras.RAS_FP32])
     assert d < 1e-3
+
+
+@pytest.mark.parametrize("prec", [ras.RAS_FP64, ras.RAS_FP32])
+def test_config3_geometry_iterates_match_oracle(prec):
+    # the config-3 subdomain shape at a size the oracle iterates in well under
+    # a second: 3D Poisson 40^3 in 12 BFS-growth parts of 3935..6459 points
+    # (config 3: 4096 +- 30 %), overlap 1, ILU(0)-PCG with 10 steps; the
+    # synchronous iterates 1..3 element by element: FP64 within 1e-9 (dot
+    # products and level-scheduled sweeps reduce in another order), FP32
+    # within 4 x the oracle's own FP32-vs-FP64 gap
+    N, P, m = 40, 12, 10
+    A = problems.poisson3d(N)
+    b = problems.rhs_uniform(A.n, 3)
+    part = ras.ras_partition_bfs(A, P, 3)
+    assert np.array_equal(part, oracle.partition_bfs(A, P, 3))
+    ctx = ras.ras_setup(A, part, P, 1, ras.RAS_LOCAL_ILU0_CG, prec, m)
+    for k in (1, 2, 3):
+        x, info = solve(ctx, A, b, ras.RAS_SYNC, max_updates=k)
+        assert info.iterations == k
+        xo64 = oracle.ras_sync(A, b, part, P, 1, oracle.ILU0_CG, oracle.FP64, m, tol=0.0,
+                               max_iter=k, nthreads=8, allow_noconv=True)[0]
+        scale = np.abs(xo64).max()
+        if prec == ras.RAS_FP64:
+            assert np.abs(x - xo64).max() <= 1e-9 * scale, k
+        else:
+            xo32 = oracle.ras_sync(A, b, part, P, 1, oracle.ILU0_CG, oracle.FP32, m, tol=0.0,
+                                   max_iter=k, nthreads=8, allow_noconv=True)[0]
+            gap = np.abs(xo32 - xo64).max()
+            assert 0.0 < gap <= 1e-4 * scale
+            assert np.abs(x - xo32).max() <= 4.0 * gap + 1e-7 * scale, (k, gap)
+    ras.ras_destroy(ctx)
