@@ -504,7 +504,7 @@ ras_status plan_launch(LaunchPlan &pl, int kind, int prec, const std::vector<Ite
   CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (nt_pref <= 0) nt_pref = (int)env_int("RAS_CTA_THREADS", 0);  // 0: per-kind default
-  pl.nt = main_threads(kind, nt_pref);
+  pl.nt = main_threads(kind, prec, nt_pref);
   pl.Wmax = Wmax;
   pl.npad_max = npad_max;
   pl.kmax = kmax;

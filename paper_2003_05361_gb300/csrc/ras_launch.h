@@ -24,7 +24,7 @@ struct LayoutJob {
 };
 
 size_t main_smem_bytes(int kind, int prec, int nt, int Wmax, int npad_max, int kmax, int nstages);
-int main_threads(int kind, int nt_pref);
+int main_threads(int kind, int prec, int nt_pref);
 int main_occupancy(int kind, int prec, int nt, size_t smem);
 cudaError_t launch_main(int kind, int prec, int nt, const Launch &L, int grid, size_t smem,
                         cudaStream_t stream);

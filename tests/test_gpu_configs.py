@@ -100,15 +100,17 @@ def test_config4_full_size():
     assert d < 1e-3
 
 
-@pytest.mark.parametrize("prec", [ras.RAS_FP64, ras.RAS_FP32])
-def test_config3_geometry_iterates_match_oracle(prec):
+@pytest.mark.parametrize("prec,N", [(ras.RAS_FP32, 40), (ras.RAS_FP64, 32)])
+def test_config3_geometry_iterates_match_oracle(prec, N):
     # the config-3 subdomain shape at a size the oracle iterates in well under
     # a second: 3D Poisson 40^3 in 12 BFS-growth parts of 3935..6459 points
-    # (config 3: 4096 +- 30 %), overlap 1, ILU(0)-PCG with 10 steps; the
+    # (config 3: 4096 +- 30 %), overlap 1, ILU(0)-PCG with 10 steps in FP32,
+    # the config's precision; FP64 on 32^3 (parts of ~2700 points: the FP64
+    # kernel keeps five local vectors in shared memory, up to ~5600 rows). The
     # synchronous iterates 1..3 element by element: FP64 within 1e-9 (dot
     # products and level-scheduled sweeps reduce in another order), FP32
     # within 4 x the oracle's own FP32-vs-FP64 gap
-    N, P, m = 40, 12, 10
+    P, m = 12, 10
     A = problems.poisson3d(N)
     b = problems.rhs_uniform(A.n, 3)
     part = ras.ras_partition_bfs(A, P, 3)
