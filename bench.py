@@ -234,11 +234,13 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline model
 
-def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
+def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged, col_bytes=2, grid=False):
     """Algorithmic bytes of one local update of each subdomain:
-    residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p,
-    local CG = nnz(A_p) (s_v + 2), once when A_p is staged in shared memory,
-    m times when it is re-read every step; ILU(0)-PCG = 2 nnz(A_p) (s + 2) m
+    residual = nnz(rows of Omega_p) (8 + 4) + 4 (n_p + 1) + 8 (n_p + |E_p|) + 8 n_p
+    (grid layout, where every column is computed: nnz 8 + 8 (n_p + |E_p|) + 8 n_p),
+    local CG = nnz(A_p) (s_v + c), once when A_p is staged in shared memory,
+    m times when it is re-read every step (c = 2 bytes of int16 column per
+    entry, 0 in the diagonal-offset form); ILU(0)-PCG = 2 nnz(A_p) (s + 2) m
     (A_p and the factors every step); band = 2 n_p (w_p + 1) s_f (the L
     and L^T, or L and U, bands);
     update = 8 |O_p| written."""
@@ -255,9 +257,12 @@ def subdomain_bytes(A, ras, ctx, kind, prec_bytes, m, staged):
         starts, ends = rp[om], rp[om + 1]
         idx = np.concatenate([np.arange(s, e) for s, e in zip(starts, ends)])
         nnz_p = int(inside[ci[idx]].sum())
-        res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
+        if grid:
+            res = nnz_rows * 8 + 8 * (n_p + e_p) + 8 * n_p
+        else:
+            res = nnz_rows * 12 + 4 * (n_p + 1) + 8 * (n_p + e_p) + 8 * n_p
         if kind == ras.RAS_LOCAL_CG:
-            loc = nnz_p * (prec_bytes + 2) * (1 if staged else m)
+            loc = nnz_p * (prec_bytes + col_bytes) * (1 if staged else m)
         elif kind == ras.RAS_LOCAL_ILU0_CG:
             # A_p and the ILU(0) factors (same pattern) read every PCG step
             loc = 2 * nnz_p * (prec_bytes + 2) * m
@@ -417,8 +422,11 @@ def run_ours(args):
     info = infos[len(infos) // 2]
     counts = ras.ras_get_update_counts(ctxs[head_prec])
     launch = ras.ras_get_launch(ctxs[head_prec])
-    staged = launch["kernel_variant"] == 3
-    per_upd = subdomain_bytes(A, ras, ctxs[head_prec], ras.RAS_LOCAL_CG, 4, M_INNER, staged)
+    staged = launch["kernel_variant"] in (3, 5)
+    dia = launch["kernel_variant"] == 5  # diagonal-offset form: no column bytes
+    # diagonal-offset form: grid layout, no column or index bytes
+    per_upd = subdomain_bytes(A, ras, ctxs[head_prec], ras.RAS_LOCAL_CG, 4, M_INNER, staged,
+                              col_bytes=0 if dia else 2, grid=dia)
     alg_bytes = float(np.dot(counts, per_upd))
     kernel_s = info.kernel_ms / 1e3
     achieved = alg_bytes / kernel_s / 1e9
@@ -426,8 +434,9 @@ def run_ours(args):
     tpu = profile_traffic("async_fp32")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": (tpu * float(counts.sum())) if tpu else None,
-            "kernel": ("ras_main_kernel<CG staged in shared memory, float, %d>" if staged else
-                       "ras_main_kernel<CG, float, %d>") % launch["cta_threads"],
+            "kernel": ("ras_main_kernel<CG staged in shared memory%s, float, %d>"
+                       % (" (diagonal-offset form)" if dia else "", launch["cta_threads"])
+                       if staged else "ras_main_kernel<CG, float, %d>" % launch["cta_threads"]),
             "kernel_ms": info.kernel_ms,
             "algorithmic_bytes": alg_bytes, "peak_source": peak_src}
 

@@ -205,6 +205,10 @@ struct ras_ctx {
   int16_t *d_lcol16 = nullptr;
   float *d_vpair = nullptr;     // staged CG, paired layout
   uint32_t *d_cpair = nullptr;
+  float *d_vdia = nullptr;      // staged CG, diagonal-offset form
+  bool dia = false;
+  int grid = 0;                 // SysDesc::grid, gs2, gs3
+  int32_t gs2 = 0, gs3 = 0;
   int32_t *d_own_g = nullptr;
   int32_t *d_gidx = nullptr, *d_rcol = nullptr, *d_own = nullptr, *d_lcol = nullptr,
           *d_levp = nullptr, *d_levr = nullptr, *d_nbr = nullptr, *d_tnbr = nullptr;
@@ -307,7 +311,80 @@ struct SubMaps {
   std::vector<int32_t> iface;   // ascending
   std::vector<int32_t> nbr;     // neighbouring subdomains (ascending, != p)
   int w = 0;                    // half-bandwidth of A_p in local order
+  // local rows on a grid box (grid_embed): global id of local row i, -1 for
+  // an inert hole row, and the local row of omega[t]; empty: row i = omega[i]
+  std::vector<int32_t> slot_g, slot_of;
+  int dims = 0;                 // grid dimension seen from Omega_p's rows (2, 3)
+  int64_t s2 = 0, s3 = 0;       // global strides of y and z
+  int32_t g0 = 0, bx = 0, bxy = 0;  // box origin (global id), row and plane lengths
 };
+
+// Lays the local rows of Omega_p out on the bounding box of Omega_p in grid
+// coordinates when A is a 2D or 3D stencil in lexicographic order: the
+// distinct distances |c - g| of the entries of Omega_p's rows are 1, s2 (and
+// s3) with s2 | s3, and each entry moves one unit along one axis of
+// x = g mod s2, y = (g / s2) mod (s3 / s2), z = g / s3. Local row
+// ((z - z0) Wy + (y - y0)) Wx + (x - x0) then keeps the order of the global
+// ids, and every entry of A_p sits at one of the fixed local offsets +-1,
+// +-Wx, +-Wx Wy; box points outside Omega_p become hole rows (the corners
+// that the breadth-first overlap leaves out). Returns false (m unchanged)
+// when the pattern is not such a stencil, or the box has more than
+// max_rows rows or over 1.25 |Omega_p|.
+bool grid_embed(const ras_csr *A, SubMaps &m, int max_rows) {
+  std::vector<int64_t> dist;
+  for (int g : m.omega)
+    for (int k = A->row_ptr[g]; k < A->row_ptr[g + 1]; ++k) {
+      const int64_t d = std::abs((int64_t)A->col_idx[k] - g);
+      if (d != 0 && std::find(dist.begin(), dist.end(), d) == dist.end()) {
+        if (dist.size() == 3) return false;
+        dist.push_back(d);
+      }
+    }
+  std::sort(dist.begin(), dist.end());
+  if (dist.size() < 2 || dist[0] != 1) return false;  // 1D: Omega_p is already contiguous
+  const bool three = dist.size() == 3;
+  const int64_t s2 = dist[1], s3 = three ? dist[2] : 0;
+  if (three && s3 % s2 != 0) return false;
+  auto coord = [&](int64_t g, int64_t *x) {
+    x[0] = g % s2;
+    x[1] = three ? (g / s2) % (s3 / s2) : g / s2;
+    x[2] = three ? g / s3 : 0;
+  };
+  int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1}, a[3], b[3];
+  for (int g : m.omega) {
+    coord(g, a);
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], a[q]);
+      hi[q] = std::max(hi[q], a[q]);
+    }
+    for (int k = A->row_ptr[g]; k < A->row_ptr[g + 1]; ++k) {
+      coord(A->col_idx[k], b);
+      int64_t moved = 0;
+      for (int q = 0; q < 3; ++q) moved += std::abs(b[q] - a[q]);
+      if (moved > 1) return false;  // wraps around a grid line or plane
+    }
+  }
+  const int64_t wx = hi[0] - lo[0] + 1, wy = hi[1] - lo[1] + 1, wz = hi[2] - lo[2] + 1;
+  const int64_t box = wx * wy * wz, n = (int64_t)m.omega.size();
+  if (box > max_rows || 4 * box > 5 * n) return false;
+  // every box point, holes included, must be a row of A
+  if (hi[0] + hi[1] * s2 + hi[2] * s3 >= A->n) return false;
+  m.dims = three ? 3 : 2;
+  m.s2 = s2;
+  m.s3 = s3;
+  m.g0 = (int32_t)(lo[0] + lo[1] * s2 + lo[2] * s3);
+  m.bx = (int32_t)wx;
+  m.bxy = (int32_t)(wx * wy);
+  m.slot_g.assign(box, -1);
+  m.slot_of.resize(n);
+  for (int64_t t = 0; t < n; ++t) {
+    coord(m.omega[t], a);
+    const int64_t sl = ((a[2] - lo[2]) * wy + (a[1] - lo[1])) * wx + (a[0] - lo[0]);
+    m.slot_g[sl] = m.omega[t];
+    m.slot_of[t] = (int32_t)sl;
+  }
+  return true;
+}
 
 // Omega_p by breadth-first layers from O_p over the graph of A (Fig. 1: one
 // layer per unit of overlap); E_p = points outside Omega_p adjacent to it.
@@ -586,6 +663,10 @@ SysDesc make_sysdesc(const ras_ctx *c, const double *b, double *x, double tol) {
   s.lcol16 = c->d_lcol16;
   s.vpair = c->d_vpair;
   s.cpair = c->d_cpair;
+  s.vdia = c->d_vdia;
+  s.grid = c->grid;
+  s.gs2 = c->gs2;
+  s.gs3 = c->gs3;
   s.lval = c->d_lval;
   s.ilu_fcol = c->d_ifc;
   s.ilu_fval = c->d_ifv;
@@ -771,6 +852,37 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     for (auto &t : th) t.join();
   }
 
+  // ---- local CG on a 2D / 3D stencil: local rows on grid boxes (all
+  // subdomains or none), so that the residual gather computes every column
+  // instead of loading it and the staged kernel can take A_p in diagonal-
+  // offset form. A staged-size problem keeps its boxes within the staged limit
+  if (kind == RAS_LOCAL_CG && (K == 5 || K == 7) && env_int("RAS_CG_GRID", 1) != 0) {
+    size_t nmax = 0;
+    for (int p = 0; p < P; ++p) nmax = std::max(nmax, maps[p].omega.size());
+    const int max_rows =
+        prec == RAS_FP32 && nmax <= (size_t)kStagedRows ? kStagedRows : INT32_MAX;
+    std::atomic<int> fail(0);
+    parallel_for(P, [&](int p) {
+      if (!fail && !grid_embed(A, maps[p], max_rows)) fail = 1;
+    });
+    for (int p = 1; p < P && !fail; ++p)
+      if (maps[p].dims != maps[0].dims || maps[p].s2 != maps[0].s2 || maps[p].s3 != maps[0].s3)
+        fail = 1;
+    if (!fail && (K < 1 + 2 * maps[0].dims ||
+                  (int64_t)n + std::max(maps[0].s2, maps[0].s3) >= INT32_MAX))
+      fail = 1;
+    if (fail) {
+      for (int p = 0; p < P; ++p) {
+        maps[p].slot_g.clear();
+        maps[p].slot_of.clear();
+      }
+    } else {
+      c->grid = maps[0].dims;
+      c->gs2 = (int32_t)maps[0].s2;
+      c->gs3 = (int32_t)maps[0].s3;
+    }
+  }
+
   // ---- descriptors and offsets
   c->subs.resize(P);
   c->cost.resize(P);
@@ -780,7 +892,10 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
   for (int p = 0; p < P; ++p) {
     SubDesc &d = c->subs[p];
     const SubMaps &mp = maps[p];
-    d.n = (int32_t)mp.omega.size();
+    d.n = (int32_t)(mp.slot_g.empty() ? mp.omega.size() : mp.slot_g.size());
+    d.g0 = mp.g0;
+    d.bx = mp.bx;
+    d.bxy = mp.bxy;
     d.npad = (d.n + 31) / 32 * 32;
     d.n_own = (int32_t)owned_lists[p].size();
     d.W = (std::max(mp.w, 1) + 3) / 4 * 4;  // band records: W a multiple of 4
@@ -846,11 +961,25 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     std::vector<int32_t> lrp, lci;
     std::vector<double> lva;
     if (kind == RAS_LOCAL_ILU0_CG) lrp.push_back(0);
+    const bool emb = !mp.slot_g.empty();
     for (int i = 0; i < d.n; ++i) {
-      const int g = mp.omega[i];
+      if (emb && mp.slot_g[i] < 0) {
+        // hole row of a grid box: flag 2, zero values, columns on itself
+        gidx[ro + i] = mp.omega[0];
+        ownf[ro + i] = 2;
+        for (int k = 0; k < K; ++k) {
+          rcol[ro * K + (int64_t)k * d.npad + i] = mp.omega[0];
+          lcol[ro * K + (int64_t)k * d.npad + i] = i;
+        }
+        continue;
+      }
+      const int t = emb ? (int)(std::lower_bound(mp.omega.begin(), mp.omega.end(), mp.slot_g[i]) -
+                                mp.omega.begin())
+                        : i;
+      const int g = mp.omega[t];
       gidx[ro + i] = g;
-      ownf[ro + i] = mp.owned[i];
-      if (mp.owned[i]) own[d.own_off + t_own++] = i;
+      ownf[ro + i] = mp.owned[t];
+      if (mp.owned[t]) own[d.own_off + t_own++] = i;
       int k = 0, kl = 0, diag_kl = -1;
       int64_t diag_lva = -1;
       double ext = 0.0;  // couplings of row i to points outside Omega_p
@@ -858,7 +987,8 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         const int col = A->col_idx[e];
         rcol[ro * K + (int64_t)k * d.npad + i] = col;
         rval[ro * K + (int64_t)k * d.npad + i] = A->val[e];
-        const int j = local_index(mp.omega, col);
+        int j = local_index(mp.omega, col);
+        if (emb && j >= 0) j = mp.slot_of[j];
         if (j < 0) {
           ext += A->val[e];
           continue;
@@ -893,6 +1023,35 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
         }
       }
       for (; k < K; ++k) rcol[ro * K + (int64_t)k * d.npad + i] = g;  // zero-valued padding
+      if (emb) {
+        // grid layout: the residual operator's entries in slot order (the
+        // diagonal, then the global offsets in ascending order), a missing
+        // entry as column g and value 0; grid_embed saw every entry of this
+        // row move one unit along one axis, so each offset has its slot
+        int64_t goff[8];
+        int ns = 0;
+        goff[ns++] = 0;
+        if (mp.dims == 3) goff[ns++] = -mp.s3;
+        goff[ns++] = -mp.s2;
+        goff[ns++] = -1;
+        goff[ns++] = 1;
+        goff[ns++] = mp.s2;
+        if (mp.dims == 3) goff[ns++] = mp.s3;
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        bool has[8] = {false, false, false, false, false, false, false, false};
+        for (int e = A->row_ptr[g]; e < A->row_ptr[g + 1]; ++e) {
+          const int64_t o = (int64_t)A->col_idx[e] - g;
+          int q = 0;
+          while (q + 1 < ns && goff[q] != o) ++q;
+          v[q] += A->val[e];
+          has[q] = true;
+        }
+        for (int q = 0; q < K; ++q) {
+          const int64_t e = ro * K + (int64_t)q * d.npad + i;
+          rcol[e] = q < ns && has[q] ? (int32_t)(g + goff[q]) : g;
+          rval[e] = q < ns ? v[q] : 0.0;
+        }
+      }
       if (!banded)
         for (; kl < K; ++kl) lcol[ro * K + (int64_t)kl * d.npad + i] = i;
       if (kind == RAS_LOCAL_ILU0_CG) lrp.push_back((int32_t)lci.size());
@@ -931,6 +1090,7 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     parallel_for(P, [&](int p) {
       const SubDesc &d = c->subs[p];
       for (int i = 0; i < d.n; ++i) {
+        if (ownf[d.row_off + i] == 2) continue;  // hole row of a grid box
         const int64_t e0 = d.row_off * K + i;
         bool found = false;
         for (int kl = 0; kl < K && !found; ++kl) {
@@ -945,6 +1105,13 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
       }
     });
     if (nodiag) return RAS_ENOTSPD;
+  }
+  // staged CG, diagonal-offset form: local rows on grid boxes whose largest
+  // local offset (bx in 2D, bxy in 3D) fits the zero margins around r
+  c->dia = c->exec_kind == kCGS && c->grid > 0 && env_int("RAS_CG_DIA", 1) != 0;
+  for (int p = 0; p < P && c->dia; ++p) {
+    const SubDesc &d = c->subs[p];
+    if ((c->grid == 3 ? d.bxy : d.bx) > kDiaMargin) c->dia = false;
   }
   std::vector<int32_t> levp_all, levr_all;
   if (kind == RAS_LOCAL_ILU0_CG) {
@@ -1105,7 +1272,36 @@ ras_status ras_setup(const ras_csr *A, const int32_t *partition, int32_t P, int3
     if (kind == RAS_LOCAL_CG && prec == RAS_FP32 && npad_max <= kStagedRows) {
       std::vector<int16_t> l16(lc.begin(), lc.end());
       if ((st = c->upload(c->d_lcol16, l16)) != RAS_OK) return st;
-      if (K % 2 == 1 && K >= 3 && K <= 7) {
+      if (c->dia) {
+        // diagonal-offset form: slot 0 the diagonal, then one slot per local
+        // offset -bxy, -bx, -1, 1, bx, bxy (2D: without +-bxy), zero where
+        // the row has no entry in Omega_p there
+        std::vector<float> vd(lval64.size(), 0.f);
+        for (int p = 0; p < P; ++p) {
+          const SubDesc &d = c->subs[p];
+          const int64_t eb = d.row_off * K, np = d.npad;
+          int loff[8], ns = 0;
+          loff[ns++] = 0;
+          if (c->grid == 3) loff[ns++] = -d.bxy;
+          loff[ns++] = -d.bx;
+          loff[ns++] = -1;
+          loff[ns++] = 1;
+          loff[ns++] = d.bx;
+          if (c->grid == 3) loff[ns++] = d.bxy;
+          for (int i = 0; i < d.n; ++i) {
+            vd[eb + i] = (float)lval64[eb + i];  // the diagonal (slot 0 of lcol)
+            for (int kl = 1; kl < K; ++kl) {
+              const int64_t e = eb + (int64_t)kl * np + i;
+              const int o = lc[e] - i;
+              if (o == 0) continue;  // padding
+              int q = 1;
+              while (q + 1 < ns && loff[q] != o) ++q;  // every local entry has its slot
+              vd[eb + (int64_t)q * np + i] += (float)lval64[e];
+            }
+          }
+        }
+        if ((st = c->upload(c->d_vdia, vd)) != RAS_OK) return st;
+      } else if (K % 2 == 1 && K >= 3 && K <= 7) {
         // paired layout for the staged kernel (diagonal first, then pairs)
         std::vector<float> vp(lval64.size(), 0.f);
         std::vector<uint32_t> cp(lval64.size() / 2 + 1, 0u);
@@ -1803,7 +1999,7 @@ ras_status ras_get_update_counts(const ras_ctx *c, int64_t *counts) {
 ras_status ras_get_launch(const ras_ctx *c, int32_t *kernel_variant, int32_t *cta_threads,
                           int32_t *grid, int32_t *inner_iters) {
   if (!c) return RAS_EINVAL;
-  if (kernel_variant) *kernel_variant = c->exec_kind;
+  if (kernel_variant) *kernel_variant = c->exec_kind == kCGS && c->dia ? 5 : c->exec_kind;
   if (cta_threads) *cta_threads = c->plan.nt;
   if (grid) *grid = c->plan.grid;
   if (inner_iters) *inner_iters = c->ls.inner_iters;

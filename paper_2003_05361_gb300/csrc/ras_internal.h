@@ -53,6 +53,12 @@ struct SubDesc {
   int32_t n_nbr;
   int32_t tnbr_off;  // neighbours in a spanning tree of the subdomain graph (tnbr[])
   int32_t n_tnbr;
+  // local rows on a grid box (SysDesc::grid > 0): box point (x, y, z) is
+  // local row x + y bx + z bxy and global id g0 + x + y gs2 + z gs3
+  int32_t g0;
+  int32_t bx;
+  int32_t bxy;
+  int32_t pad_;
 };
 
 struct SubState {
@@ -98,12 +104,20 @@ struct SysDesc {
   int32_t n;
   int32_t P;
   int32_t K;     // ELL width
-  int32_t pad_;
+  // 2 or 3: A is a 2D / 3D stencil in lexicographic order (global strides
+  // gs2, gs3) and every subdomain's local rows lie on a grid box (SubDesc g0,
+  // bx, bxy; hole rows flagged in ownf); rcol / rval then hold each row's
+  // entries in slot order: the diagonal, then the global offsets -gs3, -gs2,
+  // -1, 1, gs2, gs3 (2D: without +-gs3), a missing entry as column g and
+  // value 0. 0: the general layout
+  int32_t grid;
   double tol2;
   const SubDesc *subs;
   SubState *sub;
   SysState *st;
   const int32_t *gidx;
+  // per local row: 1 owned (O_p), 0 overlap, 2 hole row (local rows laid out
+  // on a grid box: no point of Omega_p, residual and values zero)
   const uint8_t *ownf;
   const int32_t *rcol;
   const double *rval;
@@ -119,6 +133,14 @@ struct SysDesc {
   // two int16 in one 32-bit word. Null when the plain ELL form is used.
   const float *vpair;
   const uint32_t *cpair;
+  // staged CG, diagonal-offset form (grid > 0, largest local offset, bx in
+  // 2D and bxy in 3D, at most kDiaMargin): per
+  // subdomain K arrays of npad values of A_p, the diagonal first, then one
+  // array per local offset -bxy, -bx, -1, 1, bx, bxy (2D: without +-bxy; zero
+  // where a row has no entry in Omega_p there, unused slots zero with offset
+  // 0). The kernel reads r[i + offset] and needs no column indices. Null
+  // otherwise.
+  const float *vdia;
   const void *lval;
   // ILU(0) factors in level order: forward sweep row e (lev_rows, forward
   // part) has its strictly lower entries at ilu_fcol / ilu_fval[k*npad + e]
@@ -141,6 +163,8 @@ struct SysDesc {
   // row i at row_off * kry_ld + q * npad + i); kry_ld - 1 bounds the steps
   void *kry;
   int32_t kry_ld;
+  int32_t gs2;  // grid strides (grid > 0)
+  int32_t gs3;
   int32_t pad2_;
 };
 
@@ -155,6 +179,8 @@ constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
 constexpr int kMaxEll = 8;      // ELL widths up to this are fully unrolled
 constexpr int kIluHalf = 4;     // ILU(0): strictly lower / upper entries per row kept in registers
 constexpr int kStagedRows = 6144;  // largest subdomain of the staged CG variant
+constexpr int kDiaMargin = 512;    // staged CG, diagonal-offset form: largest |offset|
+                                   // (zero margins of this many values around r)
 constexpr int kMaxBandW = 160;     // banded Cholesky: largest half-bandwidth
 constexpr int kMaxBandLuW = 112;   // banded LU: largest half-bandwidth (factorisation window
                                    // of (w+1) x (2w+1) FP64 values in shared memory)

@@ -572,9 +572,10 @@ __global__ void __launch_bounds__(128) ras_init_kernel(Launch L) {
   const SubDesc D = S.subs[it.p];
   double a = 0.0, o = 0.0;
   for (int i = threadIdx.x; i < D.n; i += 128) {
-    const double v = S.b[S.gidx[D.row_off + i]];
+    const uint8_t f = S.ownf[D.row_off + i];  // 1 owned, 0 overlap, 2 hole row
+    const double v = f == 2 ? 0.0 : S.b[S.gidx[D.row_off + i]];
     a += v * v;
-    if (S.ownf[D.row_off + i]) o += v * v;
+    if (f == 1) o += v * v;
   }
   block_sum2<128>(a, o, red);
   if (threadIdx.x == 0) {
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(128) ras_residual_kernel(Launch L) {
   const int64_t eb = D.row_off * K;
   double o = 0.0, dummy = 0.0;
   for (int i = threadIdx.x; i < D.n; i += 128) {
-    if (!S.ownf[D.row_off + i]) continue;
+    if (S.ownf[D.row_off + i] != 1) continue;
     double r = S.b[S.gidx[D.row_off + i]];
     for (int k = 0; k < K; ++k) {
       const int64_t e = eb + (int64_t)k * D.npad + i;
@@ -831,27 +832,32 @@ __device__ void cg_solve(const int32_t *lc, const T *lv, int K, int n, int npad,
 }
 
 // Two deterministic block sums with one barrier: callers alternate between
-// two buffers of 2 NT/32 values (see block_sum_1b).
+// two buffers of 2 NT/32 values (see block_sum_1b). The warp partials are
+// stored as (a, b) pairs; after the barrier every warp reads them with one
+// load (lane l takes pair l mod NT/32) and finishes with a butterfly over
+// NT/32 lanes, so each thread does one shared load instead of NT/16, and
+// every lane of every warp ends with the same bits (each butterfly level adds
+// the same two values in both lanes of a pair).
 template <int NT>
 __device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
+  constexpr int NW = NT / 32;
+  static_assert(NW >= 1 && NW <= 32 && (NW & (NW - 1)) == 0, "power-of-two warp count");
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
     b += __shfl_xor_sync(0xffffffffu, b, o);
   }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = a;
-    red[NT / 32 + (threadIdx.x >> 5)] = b;
-  }
+  float2 *red2 = reinterpret_cast<float2 *>(red);
+  if ((threadIdx.x & 31) == 0) red2[threadIdx.x >> 5] = make_float2(a, b);
   __syncthreads();
-  float sa = red[0], sb = red[NT / 32];
+  float2 v = red2[threadIdx.x & (NW - 1)];
 #pragma unroll
-  for (int i = 1; i < NT / 32; ++i) {
-    sa += red[i];
-    sb += red[NT / 32 + i];
+  for (int o = NW / 2; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
   }
-  a = sa;
-  b = sb;
+  a = v.x;
+  b = v.y;
 }
 
 // m steps of CG on A_p d = r from d = 0 in the Chronopoulos-Gear
@@ -860,22 +866,48 @@ __device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
 //   p = r + beta p, s = w + beta s, d += alpha p, r -= alpha s,
 //   w = A r, gamma' = (r, r), delta' = (w, r)   (one fused reduction),
 //   beta' = gamma'/gamma, alpha' = gamma' / (delta' - beta' gamma'/alpha).
-// A_p is staged in shared memory (FP32 values, int16 local columns, the
-// diagonal first in every row; PAIRED: the off-diagonal values and columns in
-// pairs, one 64-bit and one 32-bit load per two entries). r lives in shared memory (the operand of the
-// products, read once per step per row and reused); p, s, d, w live in
-// registers: thread t owns rows t, t + NT, ... On entry r holds the local
-// residual (zero beyond n); on exit it holds d. KC > 0 is the ELL width known
-// at compile time (KC = 0: runtime K). red holds 4 * NT/32 floats.
-template <int NT, int RMAX, int KC, bool PAIRED>
+// A_p is staged in shared memory (FP32 values, the diagonal first in every
+// row) in one of three forms: ELL with int16 local columns; PAIRED, the
+// off-diagonal values and columns in pairs (one 64-bit and one 32-bit load
+// per two entries); DIA, local rows on a grid box with row length bx and
+// plane size bxy (grid3: a 3D box), one value array per local offset (the
+// diagonal, then -bxy, -bx, -1, 1, bx, bxy; 2D without +-bxy) and no columns
+// (entry e of row i multiplies r[i + offset e]; r has zero margins of
+// kDiaMargin values on both sides, the front one cleared by the caller). r lives in shared memory (the operand of the products, read once
+// per step per row and reused); p, s, d, w live in registers: thread t owns
+// rows t, t + NT, ... On entry r holds the local residual (zero beyond n); on
+// exit it holds d. KC > 0 is the ELL width known at compile time (KC = 0:
+// runtime K). red holds 4 * NT/32 floats.
+template <int NT, int RMAX, int KC, bool PAIRED, bool DIA = false>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
-                                int m, float *r, float *red) {
+                                int m, float *r, float *red, int bx = 0, int bxy = 0,
+                                bool grid3 = false) {
   static_assert(!PAIRED || (KC > 0 && KC % 2 == 1), "pairs need an odd compile-time width");
+  static_assert(!DIA || (KC > 0 && !PAIRED), "the diagonal-offset form needs a compile-time width");
   const int tid = threadIdx.x;
   float *red0 = red, *red1 = red + 2 * (NT / 32);
   const float2 *vp = reinterpret_cast<const float2 *>(sval + npad);
   const uint32_t *cp = reinterpret_cast<const uint32_t *>(scol);
   float p[RMAX], s[RMAX], d[RMAX], w[RMAX];
+  static_assert(!DIA || KC == 5 || KC == 7, "grid stencils have 5 or 7 entries");
+  int off[DIA ? KC : 1];
+  if constexpr (DIA) {
+    if constexpr (KC == 5) {
+      off[1] = -bx;
+      off[2] = -1;
+      off[3] = 1;
+      off[4] = bx;
+    } else {
+      off[1] = grid3 ? -bxy : -bx;
+      off[2] = grid3 ? -bx : -1;
+      off[3] = grid3 ? -1 : 1;
+      off[4] = grid3 ? 1 : bx;
+      off[5] = grid3 ? bx : 0;
+      off[6] = grid3 ? bxy : 0;
+    }
+    // the tail margin may hold a larger subdomain's values: clear it
+    for (int i = npad + tid; i < npad + kDiaMargin; i += NT) r[i] = 0.f;
+  }
   // w = A r and the two products of r
   auto product = [&](float &gam, float &del) {
     gam = 0.f;
@@ -887,7 +919,10 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
       if (i < n) {
         const float ri = r[i];
         wi = sval[i] * ri;
-        if constexpr (PAIRED) {
+        if constexpr (DIA) {
+#pragma unroll
+          for (int e = 1; e < KC; ++e) wi += sval[e * npad + i] * r[i + off[e]];
+        } else if constexpr (PAIRED) {
 #pragma unroll
           for (int q = 0; q < (KC - 1) / 2; ++q) {
             const float2 v = vp[q * npad + i];
@@ -1294,7 +1329,7 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
         live[h] = i < n;
         const int ii = live[h] ? i : 0;
         g[h] = gidx[ii];
-        own[h] = live[h] && ownf[ii];
+        own[h] = live[h] && ownf[ii];  // no hole rows outside the grid layout
 #pragma unroll
         for (int k = 0; k < KC; ++k) cols[h][k] = rcol[(int64_t)k * npad + ii];
       }
@@ -1356,6 +1391,81 @@ __device__ __forceinline__ void gather_rows(const SysDesc &S, const SubDesc &D, 
   }
 }
 
+// The residual gather for local rows on a grid box (SysDesc::grid): local
+// row i is box point x = i mod bx, y = (i / bx) mod (bxy / bx), z = i / bxy
+// with global id g = g0 + x + y gs2 + z gs3, and rval holds the row's entries
+// in slot order (the diagonal, then the global offsets -gs3, -gs2, -1, 1, gs2,
+// gs3; 2D without +-gs3). No index is loaded: the loads of x (at g + offset,
+// clamped into [0, n) where an entry is missing and its value zero), of the
+// values, of b and of the row flag are all independent, so a row costs one
+// memory round trip instead of two. Same results as gather_rows up to the
+// order of the row's terms.
+template <int KC, typename CT, int NT>
+__device__ __forceinline__ void gather_rows_grid(const SysDesc &S, const SubDesc &D,
+                                                 const double *xcur, bool async, CT *rhs,
+                                                 double &a_loc, double &a_own) {
+  static_assert(KC == 5 || KC == 7, "grid stencils have 5 or 7 entries");
+  const int n = D.n, npad = D.npad;
+  const uint8_t *__restrict__ ownf = S.ownf + D.row_off;
+  const double *__restrict__ rval = S.rval + D.row_off * KC;
+  const double *__restrict__ bg = S.b;
+  double *__restrict__ xg = S.xg + D.row_off;
+  const int bx = D.bx, by = D.bxy / D.bx, g0 = D.g0, s2 = S.gs2, s3 = S.gs3, nmax = S.n - 1;
+  const bool g3 = S.grid == 3;
+  int goff[KC];
+  goff[0] = 0;
+  if constexpr (KC == 5) {
+    goff[1] = -s2;
+    goff[2] = -1;
+    goff[3] = 1;
+    goff[4] = s2;
+  } else {
+    goff[1] = g3 ? -s3 : -s2;
+    goff[2] = g3 ? -s2 : -1;
+    goff[3] = g3 ? -1 : 1;
+    goff[4] = g3 ? 1 : s2;
+    goff[5] = g3 ? s2 : 0;
+    goff[6] = g3 ? s3 : 0;
+  }
+  constexpr int R = 2;
+  for (int i0 = threadIdx.x; i0 < npad; i0 += R * NT) {
+    double xs[R][KC], vs[R][KC], bb[R];
+    uint8_t f[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      const int i = i0 + h * NT;
+      const int ii = i < n ? i : 0;
+      const int q = ii / bx, z = q / by;
+      const int g = min(g0 + (ii - q * bx) + (q - z * by) * s2 + z * s3, nmax);
+      f[h] = ownf[ii];
+      bb[h] = bg[g];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int c = min(max(g + goff[k], 0), nmax);
+        xs[h][k] = async ? ld_relaxed_f64(xcur + c) : __ldcg(xcur + c);
+        vs[h][k] = rval[(int64_t)k * npad + ii];
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h) {
+      const int i = i0 + h * NT;
+      if (i >= npad) continue;
+      double r = 0.0;
+      if (i < n && f[h] != 2) {
+        r = bb[h];
+#pragma unroll
+        for (int k = 0; k < KC; ++k) r -= vs[h][k] * xs[h][k];
+        if (f[h] == 1) {
+          xg[i] = xs[h][0];
+          a_own += r * r;
+        }
+        a_loc += r * r;
+      }
+      rhs[i] = (CT)r;
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // the persistent RAS kernel
 // --------------------------------------------------------------------------
@@ -1380,9 +1490,9 @@ struct Smem {
       return b;
     }
     if (KIND == kCGS) {
-      // values (FP32) | columns (int16) | p ; K <= kmax <= kMaxEll
+      // values (FP32) | columns (int16) | margin | p | margin ; K <= kmax <= kMaxEll
       const size_t vl = vec_len(npad_max);
-      return (size_t)kmax * vl * 6 + vl * 4;
+      return (size_t)kmax * vl * 6 + (vl + 2 * kDiaMargin) * 4;
     }
     if (KIND == kGMRES) return 4 * vec_len(npad_max) * sizeof(CT) + GmresSmem<CT, NT>::bytes();
     const int nv = KIND == kCG ? 4 : 5;
@@ -1432,7 +1542,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     wbuf = pbuf + 2 * NT;
   } else if (KIND == kCGS) {
     const size_t vl = SM::vec_len(L.npad_max);
-    v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6);  // p
+    v0 = reinterpret_cast<CT *>(smem + (size_t)L.kmax * vl * 6) + kDiaMargin;  // p
   } else {
     const size_t vl = SM::vec_len(L.npad_max);
     CT *base = reinterpret_cast<CT *>(smem);
@@ -1445,6 +1555,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
   }
   uint32_t gcount = 0;
   if (KIND == kCGS) {
+    // the front margin of p stays zero for the whole launch (the diagonal-
+    // offset products read it for rows without an entry at that offset)
+    for (int i = tid; i < kDiaMargin; i += NT) v0[i - kDiaMargin] = CT(0);
     if (tid == 0) {
       mbar_init(&s_mbar[0], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1478,14 +1591,16 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     if (KIND == kCGS && tid == 0) {
       // stage A_p (values, columns) while the residual is gathered
       const size_t vl = SM::vec_len(L.npad_max);
-      const bool pr = S.vpair != nullptr;
+      const bool pr = S.vpair != nullptr, dia = S.vdia != nullptr;
       const uint32_t bv = (uint32_t)((size_t)K * D.npad * 4);
-      const uint32_t bc = (uint32_t)((size_t)(pr ? K - 1 : K) * D.npad * 2);
+      const uint32_t bc = dia ? 0u : (uint32_t)((size_t)(pr ? K - 1 : K) * D.npad * 2);
       fence_proxy_async();
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_mbar[0])),
                    "r"(bv + bc)
                    : "memory");
-      if (pr) {
+      if (dia) {
+        bulk_copy_nobar_arrive(smem, S.vdia + D.row_off * K, bv, &s_mbar[0]);
+      } else if (pr) {
         bulk_copy_nobar_arrive(smem, S.vpair + D.row_off * K, bv, &s_mbar[0]);
         bulk_copy_nobar_arrive(smem + (size_t)L.kmax * vl * 4, S.cpair + D.row_off * K / 2, bc, &s_mbar[0]);
       } else {
@@ -1497,7 +1612,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
     for (int attempt = 0;; ++attempt) {
       a_loc = 0.0;
       a_own = 0.0;
-      if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
+      if (S.grid && K == 5) gather_rows_grid<5, CT, NT>(S, D, xcur, async, rhs, a_loc, a_own);
+      else if (S.grid && K == 7) gather_rows_grid<7, CT, NT>(S, D, xcur, async, rhs, a_loc, a_own);
+      else if (K == 5) gather_rows<5, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
       else if (K == 7) gather_rows<7, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
       else gather_rows<0, CT, NT>(S, D, K, xcur, async, rhs, a_loc, a_own);
       block_sum2<NT>(a_loc, a_own, s_red);
@@ -1553,7 +1670,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       float *pv = reinterpret_cast<float *>(v0);
       float *rd = reinterpret_cast<float *>(s_redc);
       constexpr int RM = (kStagedRows + NT - 1) / NT;
-      if (S.vpair && K == 5) cg_solve_staged<NT, RM, 5, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
+      if (S.vdia && K == 5)
+        cg_solve_staged<NT, RM, 5, false, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd, D.bx, D.bxy);
+      else if (S.vdia && K == 7)
+        cg_solve_staged<NT, RM, 7, false, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd, D.bx, D.bxy,
+                                                S.grid == 3);
+      else if (S.vpair && K == 5) cg_solve_staged<NT, RM, 5, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
       else if (S.vpair && K == 7) cg_solve_staged<NT, RM, 7, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
       else if (S.vpair && K == 3) cg_solve_staged<NT, RM, 3, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
       else if (K == 5) cg_solve_staged<NT, RM, 5, false>(sv, sc, K, D.n, D.npad, L.m, pv, rd);
@@ -1885,7 +2007,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
         const int64_t eb = D.row_off * K;
         double o = 0.0, dmy = 0.0;
         for (int i = tid; i < D.n; i += NT) {
-          if (!S.ownf[D.row_off + i]) continue;
+          if (S.ownf[D.row_off + i] != 1) continue;
           double r = S.b[S.gidx[D.row_off + i]];
           for (int k = 0; k < K; ++k) {
             const int64_t e = eb + (int64_t)k * D.npad + i;

@@ -105,6 +105,47 @@ def test_sync_trajectory_matches_oracle(kind, m, rtol):
     ras.ras_destroy(ctx)
 
 
+def _block_partition_3d(N):
+    # 2 x 2 blocks in (z, y), x undivided
+    z, y, _ = np.unravel_index(np.arange(N ** 3), (N, N, N))
+    return (2 * (z >= N // 2) + (y >= N // 2)).astype(np.int32)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_grid_layout_matches_general_layout(dim, monkeypatch):
+    # local CG on a stencil lays each subdomain's rows out on its grid box:
+    # hole rows where the breadth-first overlap cuts the box's corners or
+    # edges, the residual gather computing every column from the box instead
+    # of loading it, each row's terms in slot order. Against the general
+    # layout (RAS_CG_GRID=0) the synchronous FP64 iterates agree up to the
+    # order of a row's terms, and both match the oracle
+    if dim == 2:
+        A = problems.poisson2d(45)
+        P, gamma, part = 6, 3, ras.ras_partition_regular2d(45, 45, 3, 2)
+    else:
+        A = problems.poisson3d(14)
+        P, gamma, part = 4, 2, _block_partition_3d(14)
+    b = problems.rhs_uniform(A.n, 21)
+    xs = {}
+    for layout in ("grid", "general"):
+        if layout == "general":
+            monkeypatch.setenv("RAS_CG_GRID", "0")
+        ctx = ras.ras_setup(A, part, P, gamma, CG, F64, 8)
+        for k in (1, 3):
+            x, info = gpu_solve(A, b, part, P, gamma, CG, F64, 8, max_updates=k, ctx=ctx)
+            assert info.iterations == k
+            xs[layout, k] = x
+        ras.ras_destroy(ctx)
+    for k in (1, 3):
+        xo = oracle.ras_sync(A, b, part, P, gamma, oracle.CG, oracle.FP64, 8, tol=0.0,
+                             max_iter=k, allow_noconv=True)[0]
+        scale = np.abs(xo).max()
+        assert np.abs(xs["grid", k] - xs["general", k]).max() <= 1e-12 * scale, k
+        assert np.abs(xs["grid", k] - xo).max() <= 1e-9 * scale, k
+    # the two layouts really differ (another order of each row's terms)
+    assert not np.array_equal(xs["grid", 3], xs["general", 3])
+
+
 @pytest.mark.parametrize("kind", [BAND, CG, ILU])
 def test_sync_converged_matches_oracle(kind):
     N = 60
@@ -122,22 +163,33 @@ def test_sync_converged_matches_oracle(kind):
     assert np.abs(x - xo).max() <= 1e-7 * np.abs(xo).max()
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_staged_fp32_cg_iterates_match_oracle_fp32(dim):
-    # the shared-memory staged FP32 CG (Chronopoulos-Gear arrangement, entries
-    # in pairs: ELL width 5 in 2D, 7 in 3D) against the oracle's FP32 textbook
-    # CG: after 20 local steps the synchronous iterates agree to the FP32
-    # rounding the two summation orders leave; a wrong step length, sign or
-    # pairing moves them by orders of magnitude more
-    if dim == 2:
+@pytest.mark.parametrize("case", ["2d_dia", "2d_paired", "3d_bfs_paired", "3d_slab_dia"])
+def test_staged_fp32_cg_iterates_match_oracle_fp32(case, monkeypatch):
+    # the shared-memory staged FP32 CG (Chronopoulos-Gear arrangement) in its
+    # two storage forms: entries in pairs with int16 columns (ELL width 5 in
+    # 2D, 7 in 3D), and the diagonal-offset form (rectangles and boxes in
+    # lexicographic order: one value array per stencil offset, no columns),
+    # against the oracle's FP32 textbook CG: after 20 local steps the
+    # synchronous iterates agree to the FP32 rounding the two summation orders
+    # leave; a wrong step length, sign, pairing or offset moves them by orders
+    # of magnitude more
+    if case.startswith("2d"):
         A = problems.poisson2d(45)
         P, part = 6, ras.ras_partition_regular2d(45, 45, 3, 2)
-    else:
+    elif case == "3d_bfs_paired":
         A = problems.poisson3d(14)
         P, part = 4, ras.ras_partition_bfs(problems.poisson3d(14), 4, 7)
+    else:
+        N = 14
+        A = problems.poisson3d(N)
+        # two slabs along the slowest axis: boxes of 14 x 14 x 9 with overlap 2
+        P, part = 2, (np.arange(A.n) // (N * N) >= N // 2).astype(np.int32)
+    if case == "2d_paired":
+        monkeypatch.setenv("RAS_CG_DIA", "0")
     b = problems.rhs_uniform(A.n, 12)
     ctx = ras.ras_setup(A, part, P, 2, CG, F32, 20)
-    assert ras.ras_get_launch(ctx)["kernel_variant"] == 3  # the staged kernel ran
+    # the staged kernel ran, in the expected form
+    assert ras.ras_get_launch(ctx)["kernel_variant"] == (5 if case.endswith("dia") else 3)
     for k in (1, 3):
         x, info = gpu_solve(A, b, part, P, 2, CG, F32, 20, max_updates=k, ctx=ctx)
         assert info.iterations == k
