@@ -33,7 +33,7 @@ def _cuda_home() -> str:
 
 def _sources():
     srcs = [os.path.join(CSRC, f) for f in ("ras_kernels.cu", "ras_api.cpp", "ras_noalloc.cu")]
-    deps = srcs + [os.path.join(CSRC, f) for f in ("ras_internal.h", "ras_launch.h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in ("ras_internal.h", "ras_launch.h", "ras_convert.h")]
     deps.append(os.path.join(ROOT, "include", "ras.h"))
     return srcs, deps
 
