@@ -1,14 +1,13 @@
-// FP64 <-> FP32 conversions by integer arithmetic on the IEEE 754 bit
+// FP64 -> FP32 conversion by integer arithmetic on the IEEE 754 bit
 // patterns. On this GPU the FP64 unit retires about 1/64 of the FP32 and
-// integer rate, and a hardware conversion from or to double runs on it; the
-// residual gather converts every local row and the restricted update every
-// owned row, so the conversions are done on the integer units instead.
-// Both are exact restatements of IEEE 754 binary64 -> binary32 rounding to
-// nearest, ties to even, and of the (exact) binary32 -> binary64 widening,
-// for the operands that are normal in the target format and for zeros; the
-// rare rest (results below the smallest normal float, overflow, infinities,
-// NaN, float subnormals) goes to the compiler's conversion. Host and device
-// share the code, so a host test checks it bit for bit against the C cast.
+// integer rate, and a hardware conversion from double runs on it; the
+// residual gather converts every local row, so that conversion is done on
+// the integer units instead. It restates IEEE 754 binary64 -> binary32
+// rounding to nearest, ties to even, for results that are normal floats and
+// for zeros; the rare rest (results below the smallest normal float,
+// overflow, infinities, NaN) goes to the compiler's conversion. Host and
+// device share the code, so a host test checks it bit for bit against the C
+// cast.
 #pragma once
 #include <stdint.h>
 #include <string.h>
@@ -27,24 +26,6 @@ RAS_CVT_HD uint64_t cvt_bits_f64(double v) {
 #else
   uint64_t u;
   memcpy(&u, &v, 8);
-  return u;
-#endif
-}
-RAS_CVT_HD double cvt_f64_bits(uint64_t u) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)u);
-#else
-  double v;
-  memcpy(&v, &u, 8);
-  return v;
-#endif
-}
-RAS_CVT_HD uint32_t cvt_bits_f32(float v) {
-#ifdef __CUDA_ARCH__
-  return __float_as_uint(v);
-#else
-  uint32_t u;
-  memcpy(&u, &v, 4);
   return u;
 #endif
 }
@@ -74,17 +55,6 @@ RAS_CVT_HD float f64_to_f32_rn(double v) {
   const uint32_t rest = lo & 0x1fffffffu, half = 0x10000000u;
   f += (rest > half || (rest == half && (f & 1u))) ? 1u : 0u;
   return cvt_f32_bits(f);
-}
-
-// float -> double (exact).
-RAS_CVT_HD double f32_to_f64(float v) {
-  const uint32_t u = cvt_bits_f32(v);
-  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
-  const uint32_t e = (u >> 23) & 0xffu;
-  const uint32_t frac = u & 0x7fffffu;
-  if (e == 0 && frac == 0) return cvt_f64_bits(sign);  // +-0
-  if (e == 0 || e == 255) return (double)v;            // subnormal, infinity, NaN
-  return cvt_f64_bits(sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)frac << 29));
 }
 
 }  // namespace ras

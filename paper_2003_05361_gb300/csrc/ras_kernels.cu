@@ -132,13 +132,10 @@ __device__ __forceinline__ float to_ct(__nv_bfloat16 v) { return __bfloat162floa
 __device__ __forceinline__ float to_ct(float v) { return v; }
 __device__ __forceinline__ double to_ct(double v) { return v; }
 
-// The local right-hand side in the local-solve type and back: for FP32 by
-// integer arithmetic on the bit patterns (ras_convert.h), off the slow FP64
-// unit.
+// The local right-hand side in the local-solve type: for FP32 by integer
+// arithmetic on the bit patterns (ras_convert.h), off the slow FP64 unit.
 template <typename CT> __device__ __forceinline__ CT rhs_from_f64(double v) { return (CT)v; }
 template <> __device__ __forceinline__ float rhs_from_f64<float>(double v) { return f64_to_f32_rn(v); }
-template <typename CT> __device__ __forceinline__ double rhs_to_f64(CT v) { return (double)v; }
-template <> __device__ __forceinline__ double rhs_to_f64<float>(float v) { return f32_to_f64(v); }
 
 // Deterministic CTA reduction: butterfly inside each warp, then every thread
 // adds the per-warp values in the same order, so all threads hold the same
@@ -1740,7 +1737,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
         }
         double xn[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) xn[u] = xgl[li[u]] + rhs_to_f64<CT>(delta[li[u]]);
+        for (int u = 0; u < U; ++u) xn[u] = xgl[li[u]] + (double)delta[li[u]];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (t0 + u * NT < no) {

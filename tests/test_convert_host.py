@@ -1,5 +1,5 @@
-"""The integer-arithmetic FP64 <-> FP32 conversions the kernels use
-(csrc/ras_convert.h) against the C conversions, bit for bit, on the host:
+"""The integer-arithmetic FP64 -> FP32 conversion the kernels use
+(csrc/ras_convert.h) against the C conversion, bit for bit, on the host:
 random bit patterns over every exponent, every rounding case at the 29
 dropped bits (below, at and above one half, ties with an even and an odd
 kept bit), the ends of the binary32 normal range, carries into the next
@@ -34,13 +34,6 @@ static void check_d(uint64_t u) {
   ++tested;
   if (ua != ub) { if (bad < 5) printf("d2f %016llx: %08x vs %08x\n", (unsigned long long)u, ua, ub); ++bad; }
 }
-static void check_f(uint32_t u) {
-  float v; memcpy(&v, &u, 4);
-  double a = ras::f32_to_f64(v), b = (double)v;
-  uint64_t ua, ub; memcpy(&ua, &a, 8); memcpy(&ub, &b, 8);
-  ++tested;
-  if (ua != ub) { if (bad < 5) printf("f2d %08x\n", u); ++bad; }
-}
 int main(void) {
   for (int i = 0; i < 2000000; ++i) check_d(next());
   /* every binary64 exponent, with the dropped bits below / at / above half */
@@ -54,20 +47,13 @@ int main(void) {
           const uint64_t kept = k == 0 ? 0x7fffffull : k == 1 ? 0 : (next() & 0x7fffffull);
           check_d(((uint64_t)s << 63) | (e << 52) | (kept << 29) | r);
         }
-  for (int i = 0; i < 2000000; ++i) check_f((uint32_t)next());
-  for (uint32_t e = 0; e < 256; ++e)
-    for (int s = 0; s < 2; ++s) {
-      check_f(((uint32_t)s << 31) | (e << 23));
-      check_f(((uint32_t)s << 31) | (e << 23) | 1u);
-      check_f(((uint32_t)s << 31) | (e << 23) | 0x7fffffu);
-    }
   printf("%ld %ld\n", tested, bad);
   return 0;
 }
 """
 
 
-def test_conversions_match_c_casts(tmp_path):
+def test_conversion_matches_c_cast(tmp_path):
     cxx = shutil.which("g++") or shutil.which("c++")
     if cxx is None:
         pytest.skip("no C++ compiler")
@@ -78,5 +64,5 @@ def test_conversions_match_c_casts(tmp_path):
                     "-I" + os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
     tested, bad = map(int, out.split()[-2:])
-    assert tested > 5_000_000
+    assert tested > 3_000_000
     assert bad == 0, out
