@@ -179,6 +179,7 @@ constexpr int kMaxCtaSys = 64;  // distinct systems per CTA in one launch
 constexpr int kMaxEll = 8;      // ELL widths up to this are fully unrolled
 constexpr int kIluHalf = 4;     // ILU(0): strictly lower / upper entries per row kept in registers
 constexpr int kStagedRows = 6144;  // largest subdomain of the staged CG variant
+constexpr int kRegRows = 11;       // staged diagonal-offset CG: rows per thread with r in registers
 constexpr int kDiaMargin = 512;    // staged CG, diagonal-offset form: largest |offset|
                                    // (zero margins of this many values around r)
 constexpr int kMaxBandW = 160;     // banded Cholesky: largest half-bandwidth

@@ -884,17 +884,22 @@ __device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
 // rows t, t + NT, ... On entry r holds the local residual (zero beyond n); on
 // exit it holds d. KC > 0 is the ELL width known at compile time (KC = 0:
 // runtime K). red holds 4 * NT/32 floats.
-template <int NT, int RMAX, int KC, bool PAIRED, bool DIA = false>
+//
+// RREG (diagonal-offset form): each thread also keeps r of its own rows in
+// registers, so a step reads r from shared memory only at the neighbours
+// (and stores it once): 10 instead of 12 shared accesses per row and step.
+template <int NT, int RMAX, int KC, bool PAIRED, bool DIA = false, bool RREG = false>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
                                 int m, float *r, float *red, int bx = 0, int bxy = 0,
                                 bool grid3 = false) {
+  static_assert(!RREG || DIA, "own r in registers with the diagonal-offset form");
   static_assert(!PAIRED || (KC > 0 && KC % 2 == 1), "pairs need an odd compile-time width");
   static_assert(!DIA || (KC > 0 && !PAIRED), "the diagonal-offset form needs a compile-time width");
   const int tid = threadIdx.x;
   float *red0 = red, *red1 = red + 2 * (NT / 32);
   const float2 *vp = reinterpret_cast<const float2 *>(sval + npad);
   const uint32_t *cp = reinterpret_cast<const uint32_t *>(scol);
-  float p[RMAX], s[RMAX], d[RMAX], w[RMAX];
+  float p[RMAX], s[RMAX], d[RMAX], w[RMAX], rr[RREG ? RMAX : 1];
   static_assert(!DIA || KC == 5 || KC == 7, "grid stencils have 5 or 7 entries");
   int off[DIA ? KC : 1];
   if constexpr (DIA) {
@@ -923,7 +928,7 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
       const int i = tid + k * NT;
       float wi = 0.f;
       if (i < n) {
-        const float ri = r[i];
+        const float ri = RREG ? rr[RREG ? k : 0] : r[i];
         wi = sval[i] * ri;
         if constexpr (DIA) {
 #pragma unroll
@@ -955,6 +960,13 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     d[k] = 0.f;
   }
   __syncthreads();  // r complete, red buffers free
+  if constexpr (RREG) {
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) {
+      const int i = tid + k * NT;
+      rr[k] = i < n ? r[i] : 0.f;
+    }
+  }
   float gam, del;
   product(gam, del);
   block_sum2f_1b<NT>(gam, del, red0);
@@ -965,11 +977,13 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
       if (i < n) {
-        const float ri = r[i];
+        const float ri = RREG ? rr[RREG ? k : 0] : r[i];
         p[k] = ri + beta * p[k];
         s[k] = w[k] + beta * s[k];
         d[k] += alpha * p[k];
-        r[i] = ri - alpha * s[k];
+        const float rn = ri - alpha * s[k];
+        r[i] = rn;
+        if constexpr (RREG) rr[k] = rn;
       }
     }
     __syncthreads();  // r complete before the product reads neighbours
@@ -1676,7 +1690,12 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) ras_main_kernel(Laun
       float *pv = reinterpret_cast<float *>(v0);
       float *rd = reinterpret_cast<float *>(s_redc);
       constexpr int RM = (kStagedRows + NT - 1) / NT;
-      if (S.vdia && K == 5)
+      // subdomains of up to kRegRows rows per thread keep their r in registers
+      constexpr int RR = RM < kRegRows ? RM : kRegRows;
+      if (S.vdia && K == 5 && D.n <= RR * NT)
+        cg_solve_staged<NT, RR, 5, false, true, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd, D.bx,
+                                                      D.bxy);
+      else if (S.vdia && K == 5)
         cg_solve_staged<NT, RM, 5, false, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd, D.bx, D.bxy);
       else if (S.vdia && K == 7)
         cg_solve_staged<NT, RM, 7, false, true>(sv, sc, K, D.n, D.npad, L.m, pv, rd, D.bx, D.bxy,
