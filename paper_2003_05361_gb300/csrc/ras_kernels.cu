@@ -885,9 +885,10 @@ __device__ __forceinline__ void block_sum2f_1b(float &a, float &b, float *red) {
 // exit it holds d. KC > 0 is the ELL width known at compile time (KC = 0:
 // runtime K). red holds 4 * NT/32 floats.
 //
-// RREG (diagonal-offset form): each thread also keeps r of its own rows in
-// registers, so a step reads r from shared memory only at the neighbours
-// (and stores it once): 10 instead of 12 shared accesses per row and step.
+// RREG (diagonal-offset form): each thread also keeps r and the diagonal of
+// its own rows in registers, so a step reads r from shared memory only at
+// the neighbours (and stores it once): 9 instead of 12 shared accesses per
+// row and step.
 template <int NT, int RMAX, int KC, bool PAIRED, bool DIA = false, bool RREG = false>
 __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, int n, int npad,
                                 int m, float *r, float *red, int bx = 0, int bxy = 0,
@@ -899,7 +900,7 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
   float *red0 = red, *red1 = red + 2 * (NT / 32);
   const float2 *vp = reinterpret_cast<const float2 *>(sval + npad);
   const uint32_t *cp = reinterpret_cast<const uint32_t *>(scol);
-  float p[RMAX], s[RMAX], d[RMAX], w[RMAX], rr[RREG ? RMAX : 1];
+  float p[RMAX], s[RMAX], d[RMAX], w[RMAX], rr[RREG ? RMAX : 1], dg[RREG ? RMAX : 1];
   static_assert(!DIA || KC == 5 || KC == 7, "grid stencils have 5 or 7 entries");
   int off[DIA ? KC : 1];
   if constexpr (DIA) {
@@ -929,7 +930,7 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
       float wi = 0.f;
       if (i < n) {
         const float ri = RREG ? rr[RREG ? k : 0] : r[i];
-        wi = sval[i] * ri;
+        wi = (RREG ? dg[RREG ? k : 0] : sval[i]) * ri;
         if constexpr (DIA) {
 #pragma unroll
           for (int e = 1; e < KC; ++e) wi += sval[e * npad + i] * r[i + off[e]];
@@ -965,6 +966,7 @@ __device__ void cg_solve_staged(const float *sval, const int16_t *scol, int K, i
     for (int k = 0; k < RMAX; ++k) {
       const int i = tid + k * NT;
       rr[k] = i < n ? r[i] : 0.f;
+      dg[k] = i < n ? sval[i] : 0.f;
     }
   }
   float gam, del;
