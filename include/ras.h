@@ -273,8 +273,9 @@ ras_status ras_get_update_counts(const ras_ctx *ctx, int64_t *counts);
 /* Launch shape the context uses: kernel_variant 0 banded triangular solves
  * (Cholesky or LU factors), 1 CG reading A_p from global memory, 2
  * ILU(0)-PCG, 3 CG with A_p staged in shared memory, 4 GMRES, 5 CG with A_p
- * staged in shared memory in diagonal-offset form (no column indices; chosen
- * when every subdomain's entries lie on at most K diagonals); threads per
+ * staged in shared memory in diagonal-offset form (chosen for a 2D / 3D
+ * stencil in lexicographic order, whose subdomains' rows are laid out on
+ * grid boxes: no column indices); threads per
  * CTA; CTAs (one cooperative launch); CG / PCG / GMRES steps per local solve.
  * Any pointer may be NULL. */
 ras_status ras_get_launch(const ras_ctx *ctx, int32_t *kernel_variant, int32_t *cta_threads,
