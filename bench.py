@@ -872,6 +872,11 @@ def run_sweep(args):
              "bfs": ras.ras_partition_bfs(A, PX * PX, 1)}
     solvers = {"band_fp32": (ras.RAS_LOCAL_BANDCHOL, 1, (1, 2, 4, 8, 16)),
                "cg20_fp32": (ras.RAS_LOCAL_CG, M_INNER, (1, 2, 4, 8))}
+    # --sweep-only partition:local (e.g. regular2d:cg20_fp32) runs a subset
+    if args.sweep_only:
+        keep = [tuple(t.split(":")) for t in args.sweep_only.split(",")]
+        parts = {k: v for k, v in parts.items() if any(k == pk for pk, _ in keep)}
+        solvers = {k: v for k, v in solvers.items() if any(k == sk for _, sk in keep)}
     rows = []
 
     def run(ctx, mode, reps):
@@ -1060,6 +1065,9 @@ def main():
                     help="sync iterations of the config-4 band roofline launch")
     ap.add_argument("--sweep", action="store_true",
                     help="overlap / partition / detection sweep on the benchmark problem")
+    ap.add_argument("--sweep-only", default="",
+                    help="with --sweep: comma-separated partition:local pairs to run "
+                         "(e.g. regular2d:cg20_fp32)")
     ap.add_argument("--sweep-reps", type=int, default=10,
                     help="asynchronous solves per sweep point (median, min, max)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload only")
