@@ -543,7 +543,7 @@ def config3_section(dev, stream):
     shape and inner step count picked by ras_autotune, then time to 1e-8
     synchronous and asynchronous (one solve each, L2 flushed). Roofline: the
     local solve's model of 2 nnz(A_p) (s + 2) bytes per PCG step (A_p and
-    the ILU(0) factors, SURVEY's 84 m B/row at 7 nnz/row, s = 4) plus the
+    the ILU(0) factors: 84 m bytes per row at 7 nnz per row and s = 4) plus the
     residual rows and owned writes. Errors against the oracle's closed-form
     FP64 solve."""
     import torch
